@@ -282,7 +282,7 @@ int ora_solve(const ora_geometry *g, int W, int K, const double *S, const double
  * lambda_max(Sigma) of Theorem 2 and the Lipschitz bound of Sec. 4.2):
  * v_1 = 1/sqrt(d); lam_k = ||A v_k||^2 (Rayleigh quotient of A^T A at the unit
  * vector v_k); v_{k+1} = A^T A v_k / ||A^T A v_k||.  Stops when
- * |lam_k - lam_{k-1}| <= rtol * lam_k or after max_iters.  Returns lam. */
+ * |lam_k - lam_{k-1}| <= rtol * lam_k (rtol > 0) or after max_iters.  Returns lam. */
 double ora_norm_estimate(const ora_geometry *g, int max_iters, double rtol, int *iters_done)
 {
     long n = (long)g->n_views * g->n_bins;
@@ -303,7 +303,7 @@ double ora_norm_estimate(const ora_geometry *g, int max_iters, double rtol, int 
         nw = sqrt(nw);
         if (nw == 0.0) break;
         for (long p = 0; p < d; ++p) v[p] = w[p] / nw;
-        if (it > 1 && fabs(lam - prev) <= rtol * lam) break;
+        if (it > 1 && rtol > 0.0 && fabs(lam - prev) <= rtol * lam) break;
         prev = lam;
     }
     if (iters_done) *iters_done = it > max_iters ? max_iters : it;
