@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""EXACT throughput benchmark.
+
+One step = one call of ``exact_solve`` (500 extragradient iterations) on the
+512^2 fan-beam workload (720 views x 736 bins, 4 windows over 64 energies,
+BF16 counts, I0 = 1e4), inputs resident in HBM, L2 flushed before each step.
+The metric is EXACT iterations per second over all ranks; with N GPUs each rank
+runs an independent replica (the solve does not shard).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl exact|reference]
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on the same
+workload (each step one extragradient iteration; counts regenerated by the
+oracle's own projector).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+from synth import configs  # noqa: E402
+
+METRIC = "EXACT iters/s at 512^2x720 views"
+UNIT = "iter/s"
+L2_FLUSH_BYTES = 256 << 20
+SMS = 152
+L1_WORDS_PER_CLK = 32  # 128 B/clk/SM L1/shared data path = 32 FP32 words
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["exact", "reference"], default="exact")
+    p.add_argument("--config", default="C3")
+    p.add_argument("--iters", type=int, default=None, help="iterations per step (default: the workload's)")
+    p.add_argument("--cpu-baseline-iters", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-every", type=int, default=10)
+    return p.parse_args(argv)
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return rank, local, world
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, seconds_per_rank: float, world: int, device=None) -> float:
+    """Whole-job throughput of independent replicas: all units over the slowest rank's time."""
+    t = reduce_max(seconds_per_rank, world, device)
+    return units_per_rank * world / t
+
+
+# ---------------------------------------------------------------- workload
+
+def workload(cfg_name: str):
+    cfg = configs.ALL[cfg_name]
+    g = cfg["geometry"]
+    n = max(g["nx"], g["ny"])
+    seed = synth.case_seed(cfg_name)
+    e = synth.energy_grid(cfg["K"])
+    S = synth.window_partition(cfg["K"], cfg["W"]) * synth.smooth_spectrum(e, seed)[None, :]
+    mu = synth.power_law_mu(e, configs.mu_scale(n))
+    xs = synth.rasterize_ellipses(synth.random_ellipses(n, cfg["n_ellipses"], seed), g["nx"], g["ny"],
+                                  supersample=2)
+    return cfg, S, mu, xs, seed
+
+
+def describe(cfg) -> str:
+    g = cfg["geometry"]
+    beam = "fan" if g["beam"] == 1 else "parallel"
+    return (f"{cfg['name']}: {g['nx']}x{g['ny']} {beam} beam, {g['n_views']} views x {g['n_bins']} bins, "
+            f"{cfg['W']} windows over {cfg['K']} energies, {cfg['y_dtype']} counts, I0={cfg['I0']:g}")
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- reference (oracle) arm
+
+def oracle_inputs(cfg_name: str):
+    import oracle
+    cfg, S, mu, xs, seed = workload(cfg_name)
+    g = oracle.Geometry(**cfg["geometry"])
+    lam = oracle.expected_counts(oracle.forward(g, xs), S, mu, cfg["I0"])
+    y = synth.poisson_counts(lam, seed + 1)
+    if cfg["y_dtype"] == "bf16":
+        import torch
+        y = torch.from_numpy(y).to(torch.bfloat16).to(torch.float64).numpy()
+    nA, _ = oracle.norm_estimate(g, 3, 0.0)  # the step size does not change the work timed
+    eta = 1.0 / (4.0 * oracle.lipschitz(nA, S, mu, cfg["I0"], cfg["W"] * g.n_rays))
+    return oracle, cfg, g, S, mu, y, eta
+
+
+def cpu_baseline(cfg_name: str, iters: int):
+    """The oracle as it stands, timed on this host's cores for a few iterations."""
+    oracle, cfg, g, S, mu, y, eta = oracle_inputs(cfg_name)
+    oracle.solve(g, S, mu, cfg["I0"], y, eta, 1)  # warm caches / page in
+    t0 = time.perf_counter()
+    oracle.solve(g, S, mu, cfg["I0"], y, eta, iters)
+    dt = time.perf_counter() - t0
+    return {"value": iters / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{iters} extragradient iterations of the same workload (counts regenerated by the oracle's "
+                      f"projector), FP64; forward projection on all OpenMP threads, scatter adjoint on one"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    oracle, cfg, g, S, mu, y, eta = oracle_inputs(args.config)
+    x = np.zeros((g.ny, g.nx))
+    for _ in range(args.warmup):
+        x = oracle.solve(g, S, mu, cfg["I0"], y, eta, 1, x1=x).x
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x = oracle.solve(g, S, mu, cfg["I0"], y, eta, 1, x1=x).x
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded random-ellipse phantom, Poisson counts)",
+            "config": {"workload": describe(cfg), "step": "one extragradient iteration of the FP64 CPU oracle",
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"{args.steps} iterations, one per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- CUDA arm
+
+def load_traffic(kernel: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get(kernel)
+        from paper_2503_19925_gb300 import _build
+        import hashlib
+        h = hashlib.sha256()
+        for src in _build.sources():
+            h.update(open(src, "rb").read())
+        if rec and rec.get("source_sha256") == h.hexdigest():
+            return rec
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def run_exact(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2503_19925_gb300 as ex
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    cfg, S, mu, xs, seed = workload(args.config)
+    iters = args.iters or cfg["iters"]
+    I0 = cfg["I0"]
+    geom = ex.Geometry(**cfg["geometry"])
+
+    t0 = time.perf_counter()
+    plan = ex.Plan(geom, mu, S)
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    normA, norm_iters = plan.norm_estimate(max_iters=500, rtol=1e-9)
+    norm_ms = 1e3 * (time.perf_counter() - t0)
+    eta = plan.recommended_eta(I0, normA)
+
+    # synthetic counts from this path's own projector (Poisson, seeded)
+    x_true = torch.tensor(xs, dtype=torch.float32, device=dev)
+    z = plan.forward(x_true).double()
+    Sd = torch.tensor(S, dtype=torch.float64, device=dev)
+    mud = torch.tensor(mu, dtype=torch.float64, device=dev)
+    lam = I0 * torch.einsum("wk,kvb->wvb", Sd, torch.exp(-mud[:, None, None] * z.clamp_min(0)[None]))
+    gen = torch.Generator(device=dev).manual_seed(seed + rank)
+    y_dtype = torch.bfloat16 if cfg["y_dtype"] == "bf16" else torch.float32
+    y = torch.poisson(lam, generator=gen).to(y_dtype).contiguous()
+    del lam, z
+    x = torch.zeros(plan.shape_img, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        x.zero_()
+        plan.solve(y, I0, eta, iters, x=x, sync=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    gpu_uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", "") or "")
+    gpu_id = ("GPU-" + gpu_uuid) if gpu_uuid and not gpu_uuid.startswith("GPU-") else (gpu_uuid or str(local))
+    nnz = plan.nnz()
+    plan.profile_enable(args.profile_every)
+    plan.profile_read()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id) as clocks:
+        for k in range(args.steps):
+            flush.fill_(float(k))  # evict L2 (outside the timed events)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    prof = plan.profile_read()
+    plan.profile_enable(0)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_rank = sum(step_ms) / 1e3
+    t_max = reduce_max(t_rank, world, dev)
+    value = iters * args.steps * world / t_max
+
+    # reconstruction quality of the last step
+    xr = x.double().cpu().numpy()
+    rmse = float(np.sqrt(np.mean((xr - xs) ** 2)))
+    psnr = 20 * math.log10(1.0 / rmse)
+
+    # end to end through the public API with host buffers
+    y_host = y.cpu().pin_memory()
+    x_host = torch.zeros(plan.shape_img, dtype=torch.float32).pin_memory()
+    y_dev = torch.empty_like(y)
+    x_dev = torch.empty_like(x)
+    plan.solve_host(y_host, I0, eta, iters, x_host, y_dev=y_dev, x_dev=x_dev)  # warm
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x_host.zero_()
+        a.record(stream)
+        plan.solve_host(y_host, I0, eta, iters, x_host, y_dev=y_dev, x_dev=x_dev)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e_t = reduce_max(sum(e2e_ms) / 1e3, world, dev)
+    e2e_value = iters * args.steps * world / e2e_t
+
+    # roofline of the dominant kernel (the adjoint gather, both epilogues)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    adj_ms = prof["adjoint_half"][0] + prof["adjoint_full"][0]
+    adj_n = prof["adjoint_half"][1] + prof["adjoint_full"][1]
+    fwd_ms, fwd_n = prof["forward_link"]
+    adj_avg = adj_ms / max(adj_n, 1)
+    fwd_avg = fwd_ms / max(fwd_n, 1)
+    peak_gnnz = SMS * L1_WORDS_PER_CLK * sm_max * 1e6 / 1e9
+    achieved = nnz / (adj_avg * 1e-3) / 1e9
+    traffic = load_traffic("adjoint")
+    hbm_gbs = float(peaks.get("hbm_gbs", 6686.1))
+    roof = {"bound": "alu", "kernel": "k_adjoint (pixel-driven gather + extragradient epilogue)",
+            "achieved": achieved, "peak": peak_gnnz, "unit": "Gnnz/s", "frac": achieved / peak_gnnz,
+            "traffic": traffic["dram_bytes"] if traffic else None,
+            "peak_source": f"{SMS} SMs x {L1_WORDS_PER_CLK} FP32 words/clk (128 B/clk L1 path) x "
+                           f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+            "avg_launch_ms": adj_avg, "nnz_per_launch": nnz,
+            "forward": {"avg_launch_ms": fwd_avg, "achieved": nnz / (fwd_avg * 1e-3) / 1e9,
+                        "frac": nnz / (fwd_avg * 1e-3) / 1e9 / peak_gnnz},
+            "kernel_share": {k: v[0] / max(sum(q[0] for q in prof.values()), 1e-12) for k, v in prof.items()},
+            "hbm": {"algorithmic_bytes_per_launch": 4 * plan.n_rays + 3 * 4 * geom.nx * geom.ny,
+                    "achieved_gbs": (4 * plan.n_rays + 12 * geom.nx * geom.ny) / (adj_avg * 1e-3) / 1e9,
+                    "peak_gbs": hbm_gbs, "of": "measured"}}
+    roof["hbm"]["frac"] = roof["hbm"]["achieved_gbs"] / hbm_gbs
+
+    launches_per_step = 5 * iters + 5
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded random-ellipse phantom; Poisson counts from this path's projector)",
+            "config": {"workload": describe(cfg), "iters_per_step": iters, "step": "one exact_solve call",
+                       "l2": "flushed before every step (256 MiB write outside the timed events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": y.numel() * y.element_size()
+                    + x.numel() * 4, "d2h_bytes_per_step": x.numel() * 4},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks.summary(),
+            "psnr_db": psnr, "eta": eta, "normA_sq": normA, "norm_estimate": {"ms": norm_ms, "iters": norm_iters},
+            "plan_create_ms": plan_ms}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_baseline_iters)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.steps < 1 or args.warmup < 0:
+        raise SystemExit("--steps must be >= 1")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_exact(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

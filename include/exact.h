@@ -1,0 +1,213 @@
+/*
+ * exact.h -- C ABI of the EXACT hot path on one GB300 (sm_103a).
+ *
+ * EXACT is the projected extragradient method (Eq. (11)) for the monotone
+ * variational inequality with operator
+ *     F(x) = (1/m) sum_{w,i} (y_{w,i} - I0 h_w(<a_i, x>)) a_i,      Eq. (8)
+ *     h_w(t) = sum_k S[w][k] exp(-mu_k max(t, 0)),                    Eq. (7)
+ * of single-material polychromatic CT (Sec. 1.2), with a Joseph ray-driven
+ * projector standing in for the paper's Radon-derived rows a_i (Sec. 1,
+ * notation list) and m = W * n the number of (window, ray) measurements.
+ *
+ * Conventions shared by every call:
+ *  - Images are FP32 (FP64 only inside exact_norm_estimate), row-major
+ *    [ny][nx]; pixel (ix, iy) has its centre at ((ix-(nx-1)/2) p, (iy-(ny-1)/2) p)
+ *    with p = geometry.pixel.
+ *  - Sinograms are [n_views][n_bins] (bins fastest); counts are
+ *    [n_windows][n_views][n_bins], FP32 or BF16.
+ *  - View v has angle th = angle0 + v * angle_range / n_views; the source-side
+ *    unit vector is es = (cos th, sin th), the detector axis eu = (-sin th, cos th),
+ *    bin b sits at u_b = (b - (n_bins-1)/2) * bin_pitch + det_offset along eu.
+ *    Parallel beam: the ray passes through u_b * eu with direction -es.  Fan
+ *    beam: the ray joins the source R_s * es to the flat-detector point
+ *    (R_s - R_d) * es + u_b * eu  (R_s = src_to_center, R_d = src_to_det).
+ *  - A[i][(j,k)] = delta_i * max(0, 1 - |t_i(j) - k|): j runs over pixel centre
+ *    lines of the ray's driving axis (x when |dir_x| >= |dir_y|, else y),
+ *    t_i(j) is the cross-axis pixel-index coordinate of the crossing and
+ *    delta_i = p / |dir_drive|; pixels outside the image are zero.
+ *  - All device pointers are caller-owned and stay caller-owned.  A plan owns
+ *    only its ray/view tables (device memory it allocates at creation) and a
+ *    small pinned host buffer; per-call scratch lives in a caller-allocated
+ *    workspace bound with exact_plan_bind_workspace.
+ *  - Calls taking a stream enqueue work on it and return without waiting,
+ *    except exact_plan_create and exact_norm_estimate, which synchronise.
+ *    Every call validates its arguments and returns a status; none aborts,
+ *    traps or prints.  A plan is used from one host thread at a time and on
+ *    the device that was current when it was created.
+ */
+#ifndef EXACT_H
+#define EXACT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+struct CUstream_st;
+typedef struct CUstream_st *exact_stream_t;
+
+typedef enum {
+    EXACT_OK = 0,
+    EXACT_ERR_INVALID_ARG = 1, /* a pointer, size or parameter is out of range */
+    EXACT_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed */
+    EXACT_ERR_OOM = 3,         /* device or pinned memory could not be allocated */
+    EXACT_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+    EXACT_ERR_NONFINITE = 5,   /* a NaN/Inf residual norm stopped a solve */
+    EXACT_ERR_UNSUPPORTED = 6, /* valid input outside what this build handles */
+    EXACT_ERR_NO_WORKSPACE = 7 /* the call needs a bound workspace */
+} exact_status;
+
+typedef enum { EXACT_F32 = 0, EXACT_BF16 = 1 } exact_dtype;
+
+/* Scan geometry.  beam: 0 parallel, 1 fan (flat detector).  Lengths share one
+ * unit (pixel, bin_pitch, det_offset, src_to_center, src_to_det); angles are
+ * radians.  Requirements: 1 <= nx, ny <= 16384; n_views, n_bins >= 1;
+ * n_views * n_bins <= 2^31 - 1; pixel, bin_pitch > 0; for a fan beam
+ * src_to_det > src_to_center > half the image diagonal (the source stays
+ * outside the image). */
+typedef struct {
+    int beam;
+    int nx, ny;
+    double pixel;
+    int n_views;
+    double angle0, angle_range;
+    int n_bins;
+    double bin_pitch, det_offset;
+    double src_to_center, src_to_det;
+} exact_geometry;
+
+/* Energies: mu[k] > 0 is the attenuation per unit length at density 1 of
+ * energy bin k (the paper's mu_j, Sec. 1.2), 1 <= n_energy <= EXACT_MAX_ENERGY. */
+#define EXACT_MAX_ENERGY 256
+typedef struct {
+    int n_energy;
+    const double *mu;
+} exact_spectrum;
+
+/* Detector windows: S[w * n_energy + k] >= 0 is the fraction of the source
+ * intensity I0 that window w records from energy bin k, i.e. the paper's
+ * (I_w / I0) s_{w,k} (Eq. (2), Sec. 1); each window needs some S > 0.
+ * 1 <= n_windows <= 64. */
+typedef struct {
+    int n_windows;
+    const double *S;
+} exact_windows;
+
+typedef struct exact_plan *exact_plan_t;
+
+/* Build a plan: validate the parameters (Sec. 1.2: mu_k > 0, S >= 0), build
+ * the per-ray Joseph tables and per-view back-projection tables in FP64 on
+ * the host and upload them (FP32 and FP64 copies) to the current device.
+ * Copies every host input; the caller may free them afterwards.
+ * Synchronises.  *out is NULL on failure. */
+exact_status exact_plan_create(const exact_geometry *geometry, const exact_spectrum *spectrum,
+                               const exact_windows *windows, exact_plan_t *out);
+
+/* Free the plan's tables and host buffers (not the workspace).  NULL is OK.
+ * The caller must make sure no work using the plan is still in flight. */
+exact_status exact_plan_destroy(exact_plan_t plan);
+
+/* Number of rays n = n_views * n_bins and pixels d = nx * ny (either pointer
+ * may be NULL). */
+exact_status exact_plan_dims(exact_plan_t plan, long long *n_rays, long long *n_pixels);
+
+/* Bytes of device workspace the plan needs (256-byte aligned start). */
+size_t exact_plan_workspace_bytes(exact_plan_t plan);
+
+/* Bind caller-owned device memory of at least exact_plan_workspace_bytes as
+ * the plan's workspace (NULL, 0 unbinds).  The memory must stay valid while
+ * calls using it are in flight; calls on one plan share it, so they must be
+ * serialised on one stream (or synchronised). */
+exact_status exact_plan_bind_workspace(exact_plan_t plan, void *dev_ptr, size_t bytes);
+
+/* z = A x.  x: device [ny][nx] FP32; z: device [n_views][n_bins] FP32.
+ * Needs the workspace. */
+exact_status exact_forward(exact_plan_t plan, const float *x, float *z, exact_stream_t stream);
+
+/* g = A^T r, the exact transpose of exact_forward's matrix, evaluated as a
+ * deterministic pixel-driven gather (fixed order, no atomics).
+ * r: device [n_views][n_bins] FP32; g: device [ny][nx] FP32.  No workspace. */
+exact_status exact_adjoint(exact_plan_t plan, const float *r, float *g, exact_stream_t stream);
+
+/* F(x) of Eq. (8) with m = n_windows * n_rays.  y: device counts
+ * [n_windows][n_views][n_bins] of type y_dtype; I0 > 0 the source intensity;
+ * F: device [ny][nx] FP32.  Needs the workspace. */
+exact_status exact_operator(exact_plan_t plan, const float *x, const void *y, exact_dtype y_dtype,
+                            double I0, float *F, exact_stream_t stream);
+
+/* Options of exact_solve.  lo <= hi bound the box feasible set X = [lo, hi]^d
+ * (lo = 0, hi = +inf is the nonnegative orthant of Sec. 3.1; lo = -inf
+ * disables the lower bound).  If tol > 0 and check_every > 0 the solve stops
+ * after the first iteration t that is a multiple of check_every with
+ * rel_res = ||x_{t+1} - x_t|| / max(||x_t||, 1e-30) <= tol (FP64 norms).
+ * average_tail != 0 returns the mean of the iterates x_{t+1} for
+ * t >= floor(iters/2) instead of the last iterate (Sec. 3.1 averages the last
+ * half of the iterates). */
+typedef struct {
+    double lo, hi, tol;
+    int check_every;
+    int average_tail;
+} exact_solve_opts;
+
+typedef struct {
+    int iters_done;      /* iterations run */
+    double rel_res;      /* rel_res of the last iteration run (0 if none) */
+    exact_status status; /* EXACT_OK or EXACT_ERR_NONFINITE */
+} exact_solve_info;
+
+/* Default options: lo = 0, hi = +inf, tol = 0, check_every = 1, average_tail = 0. */
+exact_solve_opts exact_solve_opts_default(void);
+
+/* Projected extragradient, Eq. (11), with constant step eta:
+ *   x_{t+1/2} = P_X(x_t - eta F(x_t)),  x_{t+1} = P_X(x_t - eta F(x_{t+1/2})).
+ * y: device counts as in exact_operator; x: device [ny][nx] FP32 holding x_1
+ * on entry (projected onto X first) and the result on return; info: host
+ * struct written once the stream reaches the end of the solve (valid after
+ * synchronising the stream), may be NULL; opts NULL means the defaults.
+ * Needs the workspace. */
+exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, double I0, double eta,
+                         int iters, const exact_solve_opts *opts, float *x, exact_solve_info *info,
+                         exact_stream_t stream);
+
+/* ||A||_op^2 = lambda_max(A^T A) by FP64 power iteration on the device
+ * (Sec. 4.2 needs lambda_max(Sigma) = ||A||^2 / n for the step size of
+ * Theorem 2): v_1 = 1/sqrt(d), lam_k = ||A v_k||^2,
+ * v_{k+1} = A^T A v_k / ||A^T A v_k||, stopping when
+ * |lam_k - lam_{k-1}| <= rtol * lam_k or after max_iters (rtol = 0: exactly
+ * max_iters iterations).  Synchronises.
+ * iters_done may be NULL.  Needs the workspace. */
+exact_status exact_norm_estimate(exact_plan_t plan, int max_iters, double rtol, double *normA_sq,
+                                 int *iters_done, exact_stream_t stream);
+
+/* Step size 1/(4L) of Theorem 1 with L = I0 (normA_sq / m) sum_k mu_k sum_w S[w][k]
+ * (the Lipschitz bound of Sec. 4.2, m = n_windows * n_rays).  Host arithmetic. */
+exact_status exact_recommended_eta(exact_plan_t plan, double I0, double normA_sq, double *eta);
+
+/* Number of nonzero entries of A (pairs of ray and pixel with a positive
+ * Joseph weight), counted in FP64 on the host at plan creation: the
+ * algorithmic work of one forward or adjoint (one multiply-add per entry). */
+exact_status exact_plan_nnz(exact_plan_t plan, long long *nnz);
+
+/* Kernel timing of exact_solve, a profiling aid.  With sample_every > 0, every
+ * sample_every-th iteration (t % sample_every == 0) of the following solves on
+ * this plan records CUDA events around each of its kernels; 0 turns it off.
+ * Returns EXACT_ERR_OOM if the plan's event pool cannot be created. */
+#define EXACT_PROF_KINDS 4 /* 0 forward+link, 1 adjoint half step, 2 adjoint full step, 3 reduction */
+exact_status exact_profile_enable(exact_plan_t plan, int sample_every);
+
+/* Sum of the recorded kernel durations (ms) and number of timed launches per
+ * kind since the last read; synchronises on the recorded events, then clears
+ * them.  Either array may be NULL. */
+exact_status exact_profile_read(exact_plan_t plan, double ms[EXACT_PROF_KINDS],
+                                long long launches[EXACT_PROF_KINDS]);
+
+/* Static description of a status code. */
+const char *exact_status_string(exact_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXACT_H */

@@ -1,0 +1,729 @@
+// api.cu -- the C ABI of include/exact.h: plan construction (ray and view
+// tables built in FP64 on the host), workspace carve-up, and the entry points
+// that enqueue the kernels of k_forward.cu, k_adjoint.cu and k_util.cu.
+#include "exact_internal.h"
+
+#include <math.h>
+#include <new>
+#include <string.h>
+#include <vector>
+
+using namespace exact;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool isfin(double v) { return isfinite(v) != 0; }
+
+exact_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return EXACT_OK;
+    if (e == cudaErrorMemoryAllocation) return EXACT_ERR_OOM;
+    return EXACT_ERR_CUDA;
+}
+
+#define EXACT_TRY(expr)                                      \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return cuda_status(_e);       \
+    } while (0)
+
+exact_status check_geometry(const exact_geometry *g)
+{
+    if (!g) return EXACT_ERR_INVALID_ARG;
+    if (g->beam != 0 && g->beam != 1) return EXACT_ERR_INVALID_ARG;
+    if (g->nx < 1 || g->ny < 1 || g->nx > 16384 || g->ny > 16384) return EXACT_ERR_INVALID_ARG;
+    if (g->n_views < 1 || g->n_bins < 1) return EXACT_ERR_INVALID_ARG;
+    if ((long long)g->n_views * (long long)g->n_bins > 2147483647LL) return EXACT_ERR_INVALID_ARG;
+    if (!isfin(g->pixel) || !(g->pixel > 0.0)) return EXACT_ERR_INVALID_ARG;
+    if (!isfin(g->bin_pitch) || !(g->bin_pitch > 0.0)) return EXACT_ERR_INVALID_ARG;
+    if (!isfin(g->angle0) || !isfin(g->angle_range) || !isfin(g->det_offset)) return EXACT_ERR_INVALID_ARG;
+    if (g->beam == 1) {
+        const double half_diag = 0.5 * g->pixel * sqrt((double)g->nx * g->nx + (double)g->ny * g->ny);
+        if (!isfin(g->src_to_center) || !isfin(g->src_to_det)) return EXACT_ERR_INVALID_ARG;
+        if (!(g->src_to_center > half_diag + 2.0 * g->pixel)) return EXACT_ERR_INVALID_ARG;
+        if (!(g->src_to_det > g->src_to_center)) return EXACT_ERR_INVALID_ARG;
+    }
+    return EXACT_OK;
+}
+
+// Ray of view v, bin b: a point (px, py) on it and its unit direction (dx, dy).
+void ray_line(const exact_geometry &g, int v, int b, double &px, double &py, double &dx, double &dy)
+{
+    const double th = g.angle0 + (double)v * g.angle_range / (double)g.n_views;
+    const double c = cos(th), s = sin(th);
+    const double u = ((double)b - 0.5 * (double)(g.n_bins - 1)) * g.bin_pitch + g.det_offset;
+    if (g.beam == 0) {
+        px = -s * u;
+        py = c * u;
+        dx = -c;
+        dy = -s;
+    } else {
+        const double sx = g.src_to_center * c, sy = g.src_to_center * s;
+        const double qx = (g.src_to_center - g.src_to_det) * c - s * u;
+        const double qy = (g.src_to_center - g.src_to_det) * s + c * u;
+        const double ex = qx - sx, ey = qy - sy, len = sqrt(ex * ex + ey * ey);
+        px = sx;
+        py = sy;
+        dx = ex / len;
+        dy = ey / len;
+    }
+}
+
+struct RayHost {
+    int axis, jlo, jhi;
+    double alpha, beta, delta;
+};
+
+RayHost make_ray(const exact_geometry &g, int v, int b)
+{
+    double px, py, dx, dy;
+    ray_line(g, v, b, px, py, dx, dy);
+    RayHost r;
+    const double x0 = -0.5 * (double)(g.nx - 1) * g.pixel;
+    const double y0 = -0.5 * (double)(g.ny - 1) * g.pixel;
+    int nd, nc;
+    if (fabs(dx) >= fabs(dy)) {
+        r.axis = 0;
+        r.beta = dy / dx;
+        r.alpha = (py + (x0 - px) * r.beta) / g.pixel + 0.5 * (double)(g.ny - 1);
+        r.delta = g.pixel / fabs(dx);
+        nd = g.nx;
+        nc = g.ny;
+    } else {
+        r.axis = 1;
+        r.beta = dx / dy;
+        r.alpha = (px + (y0 - py) * r.beta) / g.pixel + 0.5 * (double)(g.nx - 1);
+        r.delta = g.pixel / fabs(dy);
+        nd = g.ny;
+        nc = g.nx;
+    }
+    // driving indices whose crossing lies in (-1.5, nc + 0.5): a superset of
+    // the samples that touch the image, half a pixel of margin for FP32 t
+    const double tlo = -1.5, thi = (double)nc + 0.5;
+    double jl, jh;
+    if (r.beta == 0.0) {
+        const bool in = r.alpha > tlo && r.alpha < thi;
+        jl = in ? 0.0 : 1.0;
+        jh = in ? (double)(nd - 1) : 0.0;
+    } else {
+        double a = (tlo - r.alpha) / r.beta, c = (thi - r.alpha) / r.beta;
+        if (a > c) {
+            const double t = a;
+            a = c;
+            c = t;
+        }
+        jl = fmax(0.0, ceil(a));
+        jh = fmin((double)(nd - 1), floor(c));
+    }
+    if (!(jl <= jh)) {
+        r.jlo = 1;
+        r.jhi = 0;
+    } else {
+        r.jlo = (int)jl;
+        r.jhi = (int)jh;
+    }
+    return r;
+}
+
+ViewRec make_view(const exact_geometry &g, int v, int flags)
+{
+    const double th = g.angle0 + (double)v * g.angle_range / (double)g.n_views;
+    const double c = cos(th), s = sin(th), p = g.pixel;
+    const double cx = 0.5 * (double)(g.nx - 1), cy = 0.5 * (double)(g.ny - 1);
+    // P.eu = -s p kx + c p ky + (cx s - cy c) p ;  P.es = c p kx + s p ky - (cx c + cy s) p
+    ViewRec r;
+    const double cc = 0.5 * (double)(g.n_bins - 1) - g.det_offset / g.bin_pitch;
+    if (g.beam == 0) {
+        const double k = 1.0 / g.bin_pitch;
+        r.n0 = (float)(k * (cx * s - cy * c) * p);
+        r.n1 = (float)(-k * s * p);
+        r.n2 = (float)(k * c * p);
+        r.d0 = 1.0f;
+        r.d1 = 0.0f;
+        r.d2 = 0.0f;
+    } else {
+        const double k = g.src_to_det / g.bin_pitch;
+        r.n0 = (float)(k * (cx * s - cy * c) * p);
+        r.n1 = (float)(-k * s * p);
+        r.n2 = (float)(k * c * p);
+        r.d0 = (float)(g.src_to_center + (cx * c + cy * s) * p);
+        r.d1 = (float)(-c * p);
+        r.d2 = (float)(-s * p);
+    }
+    r.c = (float)cc;
+    r.flags = flags;
+    return r;
+}
+
+exact_status check_plan(exact_plan_t p, bool need_ws)
+{
+    if (!p) return EXACT_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return EXACT_ERR_CUDA;
+    if (dev != reinterpret_cast<Plan *>(p)->device) return EXACT_ERR_INVALID_ARG;
+    if (need_ws && !reinterpret_cast<Plan *>(p)->ws) return EXACT_ERR_NO_WORKSPACE;
+    return EXACT_OK;
+}
+
+struct Carve {
+    size_t off = 0;
+    template <typename T>
+    T *take(char *base, size_t count)
+    {
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off = align_up(off + count * sizeof(T));
+        return p;
+    }
+};
+
+// Lays the workspace out (base == nullptr: only measures).
+size_t carve(Plan &P, char *base)
+{
+    Carve c;
+    const long long nx = P.g.nx, ny = P.g.ny;
+    for (int q = 0; q < 2; ++q) {
+        P.xr[q] = c.take<float>(base, (size_t)(ny * P.ldr()));
+        P.xc[q] = c.take<float>(base, (size_t)(nx * P.ldc()));
+    }
+    P.Y = c.take<float>(base, (size_t)P.n);
+    P.r = c.take<float>(base, (size_t)P.n);
+    const int nb_adj = adjoint_blocks(P.g.nx, P.g.ny);
+    const int nb_fwd = forward_d_blocks(P.n);
+    P.partials = c.take<double>(base, (size_t)(2 * nb_adj + nb_fwd + nb_adj));
+    P.avg = c.take<double>(base, (size_t)P.d);
+    P.xrd = c.take<double>(base, (size_t)(ny * P.ldr()));
+    P.xcd = c.take<double>(base, (size_t)(nx * P.ldc()));
+    P.zd = c.take<double>(base, (size_t)P.n);
+    P.state = c.take<DevState>(base, 1);
+    return c.off;
+}
+
+void info_copy_cb(void *data)
+{
+    auto *pair = static_cast<std::pair<const DevState *, exact_solve_info *> *>(data);
+    const DevState *s = pair->first;
+    exact_solve_info *dst = pair->second;
+    dst->iters_done = s->iters_done;
+    dst->rel_res = s->rel_res;
+    dst->status = (exact_status)s->status;
+    delete pair;
+}
+
+LinkCoef make_coef(const Plan &P, double I0)
+{
+    LinkCoef c;
+    memset(&c, 0, sizeof(c));
+    for (int k = 0; k < P.K; ++k) {
+        c.mu2[k] = P.mu_log2e[k];
+        c.c[k] = (float)(I0 * (double)P.C[k]);
+    }
+    return c;
+}
+
+ImgF img_of(const Plan &P, int q)
+{
+    ImgF im;
+    im.xr = P.xr[q];
+    im.xc = P.xc[q];
+    im.nx = P.g.nx;
+    im.ny = P.g.ny;
+    im.ldr = P.ldr();
+    im.ldc = P.ldc();
+    return im;
+}
+
+// Event pair around one sampled launch (profiling aid); returns the pair
+// index or -1 when this launch is not sampled.
+int prof_begin(Plan &P, int kind, int iter, cudaStream_t s)
+{
+    if (P.prof_every <= 0 || iter % P.prof_every != 0 || P.prof_used >= P.prof_cap) return -1;
+    const int u = P.prof_used++;
+    P.prof_kind[u] = kind;
+    if (cudaEventRecord(P.prof_ev[2 * u], s) != cudaSuccess) return -1;
+    return u;
+}
+
+void prof_end(Plan &P, int u, cudaStream_t s)
+{
+    if (u >= 0) cudaEventRecord(P.prof_ev[2 * u + 1], s);
+}
+
+void prof_free(Plan &P)
+{
+    for (int i = 0; i < 2 * P.prof_cap; ++i) cudaEventDestroy(P.prof_ev[i]);
+    delete[] P.prof_ev;
+    delete[] P.prof_kind;
+    P.prof_ev = nullptr;
+    P.prof_kind = nullptr;
+    P.prof_cap = P.prof_used = 0;
+}
+
+// Nonzero entries of A, counted tap by tap in FP64.
+long long count_nnz(const exact_geometry &g)
+{
+    long long nnz = 0;
+    for (int v = 0; v < g.n_views; ++v)
+        for (int b = 0; b < g.n_bins; ++b) {
+            const RayHost h = make_ray(g, v, b);
+            const int nc = h.axis ? g.nx : g.ny;
+            for (int j = h.jlo; j <= h.jhi; ++j) {
+                const double t = h.alpha + h.beta * (double)j;
+                const double k0 = floor(t), f = t - k0;
+                if (1.0 - f > 0.0 && k0 >= 0.0 && k0 < (double)nc) ++nnz;
+                if (f > 0.0 && k0 + 1.0 >= 0.0 && k0 + 1.0 < (double)nc) ++nnz;
+            }
+        }
+    return nnz;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *exact_status_string(exact_status s)
+{
+    switch (s) {
+    case EXACT_OK: return "ok";
+    case EXACT_ERR_INVALID_ARG: return "invalid argument";
+    case EXACT_ERR_CUDA: return "CUDA error";
+    case EXACT_ERR_OOM: return "out of memory";
+    case EXACT_ERR_TIMEOUT: return "bounded device wait timed out";
+    case EXACT_ERR_NONFINITE: return "non-finite residual";
+    case EXACT_ERR_UNSUPPORTED: return "unsupported";
+    case EXACT_ERR_NO_WORKSPACE: return "no workspace bound";
+    }
+    return "unknown status";
+}
+
+exact_solve_opts exact_solve_opts_default(void)
+{
+    exact_solve_opts o;
+    o.lo = 0.0;
+    o.hi = INFINITY;
+    o.tol = 0.0;
+    o.check_every = 1;
+    o.average_tail = 0;
+    return o;
+}
+
+exact_status exact_plan_create(const exact_geometry *geometry, const exact_spectrum *spectrum,
+                               const exact_windows *windows, exact_plan_t *out)
+{
+    if (!out) return EXACT_ERR_INVALID_ARG;
+    *out = nullptr;
+    exact_status st = check_geometry(geometry);
+    if (st != EXACT_OK) return st;
+    if (!spectrum || !windows || !spectrum->mu || !windows->S) return EXACT_ERR_INVALID_ARG;
+    const int K = spectrum->n_energy, W = windows->n_windows;
+    if (K < 1 || K > kMaxK || W < 1 || W > 64) return EXACT_ERR_INVALID_ARG;
+    for (int k = 0; k < K; ++k)
+        if (!isfin(spectrum->mu[k]) || !(spectrum->mu[k] > 0.0)) return EXACT_ERR_INVALID_ARG;
+    for (int w = 0; w < W; ++w) {
+        double sw = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double v = windows->S[w * K + k];
+            if (!isfin(v) || v < 0.0) return EXACT_ERR_INVALID_ARG;
+            sw += v;
+        }
+        if (!(sw > 0.0)) return EXACT_ERR_INVALID_ARG;
+    }
+
+    Plan *P = new (std::nothrow) Plan();
+    if (!P) return EXACT_ERR_OOM;
+    if (cudaGetDevice(&P->device) != cudaSuccess) {
+        delete P;
+        return EXACT_ERR_CUDA;
+    }
+    P->g = *geometry;
+    P->W = W;
+    P->K = K;
+    P->n = (long long)geometry->n_views * geometry->n_bins;
+    P->d = (long long)geometry->nx * geometry->ny;
+    P->Csum_mu = 0.0;
+    for (int k = 0; k < K; ++k) {
+        double ck = 0.0;
+        for (int w = 0; w < W; ++w) ck += windows->S[w * K + k];
+        P->C[k] = (float)ck;
+        P->mu_log2e[k] = (float)(spectrum->mu[k] * 1.4426950408889634);
+        P->Csum_mu += ck * spectrum->mu[k];
+    }
+
+    const exact_geometry &g = *geometry;
+    std::vector<RayF> rf((size_t)P->n);
+    std::vector<RayD> rd((size_t)P->n);
+    std::vector<ViewRec> vw((size_t)g.n_views);
+    for (int v = 0; v < g.n_views; ++v) {
+        int flags = 0;
+        for (int b = 0; b < g.n_bins; ++b) {
+            const RayHost h = make_ray(g, v, b);
+            const int bits = (h.jlo & 0x7fff) | ((h.jhi & 0x7fff) << 15) | (h.axis << 30);
+            const size_t i = (size_t)v * g.n_bins + b;
+            rf[i].alpha = (float)h.alpha;
+            rf[i].beta = (float)h.beta;
+            rf[i].delta = (float)h.delta;
+            rf[i].bits = bits;
+            rd[i].alpha = h.alpha;
+            rd[i].beta = h.beta;
+            rd[i].delta = h.delta;
+            rd[i].bits = bits;
+            rd[i].pad = 0;
+            flags |= h.axis ? 2 : 1;
+        }
+        vw[v] = make_view(g, v, flags);
+    }
+    cudaError_t e = cudaMalloc(&P->rays_f, sizeof(RayF) * rf.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->rays_d, sizeof(RayD) * rd.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->views, sizeof(ViewRec) * vw.size());
+    if (e == cudaSuccess) e = cudaMemcpy(P->rays_f, rf.data(), sizeof(RayF) * rf.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->rays_d, rd.data(), sizeof(RayD) * rd.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->views, vw.data(), sizeof(ViewRec) * vw.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMallocHost(&P->host_state, sizeof(DevState));
+    if (e != cudaSuccess) {
+        exact_plan_destroy(reinterpret_cast<exact_plan_t>(P));
+        return cuda_status(e);
+    }
+    memset(P->host_state, 0, sizeof(DevState));
+    *out = reinterpret_cast<exact_plan_t>(P);
+    return EXACT_OK;
+}
+
+exact_status exact_plan_destroy(exact_plan_t plan)
+{
+    if (!plan) return EXACT_OK;
+    Plan *P = reinterpret_cast<Plan *>(plan);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (P->device >= 0 && prev != P->device) cudaSetDevice(P->device);
+    if (P->rays_f) cudaFree(P->rays_f);
+    if (P->rays_d) cudaFree(P->rays_d);
+    if (P->views) cudaFree(P->views);
+    if (P->host_state) cudaFreeHost(P->host_state);
+    if (P->prof_ev) prof_free(*P);
+    if (prev >= 0 && prev != P->device) cudaSetDevice(prev);
+    delete P;
+    return EXACT_OK;
+}
+
+exact_status exact_plan_dims(exact_plan_t plan, long long *n_rays, long long *n_pixels)
+{
+    if (!plan) return EXACT_ERR_INVALID_ARG;
+    const Plan *P = reinterpret_cast<const Plan *>(plan);
+    if (n_rays) *n_rays = P->n;
+    if (n_pixels) *n_pixels = P->d;
+    return EXACT_OK;
+}
+
+size_t exact_plan_workspace_bytes(exact_plan_t plan)
+{
+    if (!plan) return 0;
+    Plan tmp = *reinterpret_cast<Plan *>(plan);
+    return carve(tmp, nullptr);
+}
+
+exact_status exact_plan_bind_workspace(exact_plan_t plan, void *dev_ptr, size_t bytes)
+{
+    if (!plan) return EXACT_ERR_INVALID_ARG;
+    Plan *P = reinterpret_cast<Plan *>(plan);
+    if (!dev_ptr) {
+        P->ws = nullptr;
+        P->ws_bytes = 0;
+        return EXACT_OK;
+    }
+    if (reinterpret_cast<uintptr_t>(dev_ptr) % kAlign != 0) return EXACT_ERR_INVALID_ARG;
+    if (bytes < exact_plan_workspace_bytes(plan)) return EXACT_ERR_INVALID_ARG;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, dev_ptr) != cudaSuccess || attr.type != cudaMemoryTypeDevice ||
+        attr.device != P->device) {
+        cudaGetLastError();
+        return EXACT_ERR_INVALID_ARG;
+    }
+    P->ws = dev_ptr;
+    P->ws_bytes = bytes;
+    carve(*P, static_cast<char *>(dev_ptr));
+    return EXACT_OK;
+}
+
+exact_status exact_forward(exact_plan_t plan, const float *x, float *z, exact_stream_t stream)
+{
+    exact_status st = check_plan(plan, true);
+    if (st != EXACT_OK) return st;
+    if (!x || !z) return EXACT_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    EXACT_TRY(launch_pack(x, P.xr[0], P.xc[0], P.g.nx, P.g.ny, P.ldr(), P.ldc(), 0.f, 0.f, false, s));
+    FwdArgs a;
+    memset(&a, 0, sizeof(a));
+    a.img = img_of(P, 0);
+    a.rays = P.rays_f;
+    a.n = P.n;
+    a.z = z;
+    EXACT_TRY(launch_forward(a, false, nullptr, s));
+    return EXACT_OK;
+}
+
+exact_status exact_adjoint(exact_plan_t plan, const float *r, float *g, exact_stream_t stream)
+{
+    exact_status st = check_plan(plan, false);
+    if (st != EXACT_OK) return st;
+    if (!r || !g) return EXACT_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    AdjArgs a;
+    memset(&a, 0, sizeof(a));
+    a.rays = P.rays_f;
+    a.views = P.views;
+    a.n_views = P.g.n_views;
+    a.n_bins = P.g.n_bins;
+    a.nx = P.g.nx;
+    a.ny = P.g.ny;
+    a.r = r;
+    a.scale = 1.0f;
+    a.out = g;
+    EXACT_TRY(launch_adjoint(a, ADJ_PLAIN, P.g.beam == 1, reinterpret_cast<cudaStream_t>(stream)));
+    return EXACT_OK;
+}
+
+exact_status exact_operator(exact_plan_t plan, const float *x, const void *y, exact_dtype y_dtype, double I0,
+                            float *F, exact_stream_t stream)
+{
+    exact_status st = check_plan(plan, true);
+    if (st != EXACT_OK) return st;
+    if (!x || !y || !F) return EXACT_ERR_INVALID_ARG;
+    if (y_dtype != EXACT_F32 && y_dtype != EXACT_BF16) return EXACT_ERR_INVALID_ARG;
+    if (!isfin(I0) || !(I0 > 0.0)) return EXACT_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const LinkCoef coef = make_coef(P, I0);
+    EXACT_TRY(launch_collapse(y, y_dtype, P.W, P.n, P.Y, s));
+    EXACT_TRY(launch_pack(x, P.xr[0], P.xc[0], P.g.nx, P.g.ny, P.ldr(), P.ldc(), 0.f, 0.f, false, s));
+    FwdArgs f;
+    memset(&f, 0, sizeof(f));
+    f.img = img_of(P, 0);
+    f.rays = P.rays_f;
+    f.n = P.n;
+    f.Y = P.Y;
+    f.r = P.r;
+    f.K = P.K;
+    EXACT_TRY(launch_forward(f, true, &coef, s));
+    AdjArgs a;
+    memset(&a, 0, sizeof(a));
+    a.rays = P.rays_f;
+    a.views = P.views;
+    a.n_views = P.g.n_views;
+    a.n_bins = P.g.n_bins;
+    a.nx = P.g.nx;
+    a.ny = P.g.ny;
+    a.r = P.r;
+    a.scale = (float)(1.0 / ((double)P.W * (double)P.n));
+    a.out = F;
+    EXACT_TRY(launch_adjoint(a, ADJ_PLAIN, P.g.beam == 1, s));
+    return EXACT_OK;
+}
+
+exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, double I0, double eta, int iters,
+                         const exact_solve_opts *opts, float *x, exact_solve_info *info, exact_stream_t stream)
+{
+    exact_status st = check_plan(plan, true);
+    if (st != EXACT_OK) return st;
+    if (!y || !x) return EXACT_ERR_INVALID_ARG;
+    if (y_dtype != EXACT_F32 && y_dtype != EXACT_BF16) return EXACT_ERR_INVALID_ARG;
+    if (!isfin(I0) || !(I0 > 0.0) || !isfin(eta) || !(eta > 0.0) || iters < 0) return EXACT_ERR_INVALID_ARG;
+    const exact_solve_opts o = opts ? *opts : exact_solve_opts_default();
+    if (isnan(o.lo) || isnan(o.hi) || o.lo > o.hi || o.lo == INFINITY || o.hi == -INFINITY)
+        return EXACT_ERR_INVALID_ARG;
+    if (!isfin(o.tol) || o.tol < 0.0 || o.check_every < 0) return EXACT_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const float lo = (float)o.lo, hi = (float)o.hi;
+    const LinkCoef coef = make_coef(P, I0);
+    const int avg_from = iters / 2;
+    const int nb = adjoint_blocks(P.g.nx, P.g.ny);
+
+    EXACT_TRY(launch_reset_state(P.state, s));
+    EXACT_TRY(launch_collapse(y, y_dtype, P.W, P.n, P.Y, s));
+    EXACT_TRY(launch_pack(x, P.xr[0], P.xc[0], P.g.nx, P.g.ny, P.ldr(), P.ldc(), lo, hi, true, s));
+    EXACT_TRY(cudaMemsetAsync(P.xr[1], 0, sizeof(float) * (size_t)(P.g.ny * P.ldr()), s));
+    EXACT_TRY(cudaMemsetAsync(P.xc[1], 0, sizeof(float) * (size_t)(P.g.nx * P.ldc()), s));
+    if (o.average_tail) EXACT_TRY(cudaMemsetAsync(P.avg, 0, sizeof(double) * (size_t)P.d, s));
+
+    FwdArgs f;
+    memset(&f, 0, sizeof(f));
+    f.rays = P.rays_f;
+    f.n = P.n;
+    f.Y = P.Y;
+    f.r = P.r;
+    f.K = P.K;
+    f.state = P.state;
+    AdjArgs a;
+    memset(&a, 0, sizeof(a));
+    a.rays = P.rays_f;
+    a.views = P.views;
+    a.n_views = P.g.n_views;
+    a.n_bins = P.g.n_bins;
+    a.nx = P.g.nx;
+    a.ny = P.g.ny;
+    a.r = P.r;
+    a.scale = (float)(-eta / ((double)P.W * (double)P.n));
+    a.base_r = P.xr[0];
+    a.ldr = P.ldr();
+    a.ldc = P.ldc();
+    a.lo = lo;
+    a.hi = hi;
+    a.partials = P.partials;
+    a.avg = o.average_tail ? P.avg : nullptr;
+    a.avg_from = avg_from;
+    a.state = P.state;
+    const bool fan = P.g.beam == 1;
+    int u;
+    for (int t = 0; t < iters; ++t) {
+        // half step: x_{t+1/2} = P(x_t - eta F(x_t))
+        f.img = img_of(P, 0);
+        u = prof_begin(P, 0, t, s);
+        EXACT_TRY(launch_forward(f, true, &coef, s));
+        prof_end(P, u, s);
+        a.out_r = P.xr[1];
+        a.out_c = P.xc[1];
+        a.iter = t;
+        u = prof_begin(P, 1, t, s);
+        EXACT_TRY(launch_adjoint(a, ADJ_EG, fan, s));
+        prof_end(P, u, s);
+        // full step from the same base: x_{t+1} = P(x_t - eta F(x_{t+1/2}))
+        f.img = img_of(P, 1);
+        u = prof_begin(P, 0, t, s);
+        EXACT_TRY(launch_forward(f, true, &coef, s));
+        prof_end(P, u, s);
+        a.out_r = P.xr[0];
+        a.out_c = P.xc[0];
+        u = prof_begin(P, 2, t, s);
+        EXACT_TRY(launch_adjoint(a, ADJ_EG_FINAL, fan, s));
+        prof_end(P, u, s);
+        u = prof_begin(P, 3, t, s);
+        EXACT_TRY(launch_solve_reduce(P.partials, nb, P.state, t, o.tol, o.check_every, s));
+        prof_end(P, u, s);
+    }
+    EXACT_TRY(launch_unpack(P.xr[0], P.ldr(), P.g.nx, P.g.ny, x, o.average_tail ? P.avg : nullptr, P.state,
+                            avg_from, s));
+    if (info) {
+        EXACT_TRY(cudaMemcpyAsync(P.host_state, P.state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        auto *pair = new (std::nothrow) std::pair<const DevState *, exact_solve_info *>(P.host_state, info);
+        if (!pair) return EXACT_ERR_OOM;
+        cudaError_t e = cudaLaunchHostFunc(s, info_copy_cb, pair);
+        if (e != cudaSuccess) {
+            delete pair;
+            return cuda_status(e);
+        }
+    }
+    return EXACT_OK;
+}
+
+exact_status exact_norm_estimate(exact_plan_t plan, int max_iters, double rtol, double *normA_sq, int *iters_done,
+                                 exact_stream_t stream)
+{
+    exact_status st = check_plan(plan, true);
+    if (st != EXACT_OK) return st;
+    if (!normA_sq || max_iters < 1 || !isfin(rtol) || rtol < 0.0) return EXACT_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int nb_adj = adjoint_blocks(P.g.nx, P.g.ny);
+    const int nb_fwd = forward_d_blocks(P.n);
+    double *pz = P.partials + 2 * nb_adj;
+    double *pw = pz + nb_fwd;
+    const bool fan = P.g.beam == 1;
+    EXACT_TRY(launch_power_init(P.xrd, P.xcd, P.g.nx, P.g.ny, P.ldr(), P.ldc(), P.state, s));
+    const int chunk = 8;
+    for (int it0 = 0; it0 < max_iters; it0 += chunk) {
+        const int it1 = it0 + chunk < max_iters ? it0 + chunk : max_iters;
+        for (int it = it0; it < it1; ++it) {
+            EXACT_TRY(launch_forward_d(P.rays_d, P.n, P.xrd, P.xcd, P.g.nx, P.g.ny, P.ldr(), P.ldc(), P.zd, pz,
+                                       P.state, s));
+            EXACT_TRY(launch_adjoint_d(P.rays_d, P.views, P.g.n_views, P.g.n_bins, P.g.nx, P.g.ny, P.zd, P.xrd,
+                                       P.xcd, P.ldr(), P.ldc(), pw, P.state, fan, s));
+            EXACT_TRY(launch_power_reduce(pz, nb_fwd, pw, nb_adj, P.state, it, rtol, s));
+        }
+        EXACT_TRY(cudaMemcpyAsync(P.host_state, P.state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        EXACT_TRY(cudaStreamSynchronize(s));
+        if (P.host_state->done) break;
+    }
+    if (P.host_state->status != EXACT_OK) return (exact_status)P.host_state->status;
+    *normA_sq = P.host_state->lam;
+    if (iters_done) *iters_done = P.host_state->iters_done;
+    return EXACT_OK;
+}
+
+exact_status exact_recommended_eta(exact_plan_t plan, double I0, double normA_sq, double *eta)
+{
+    if (!plan || !eta || !isfin(I0) || !(I0 > 0.0) || !isfin(normA_sq) || !(normA_sq > 0.0))
+        return EXACT_ERR_INVALID_ARG;
+    const Plan *P = reinterpret_cast<const Plan *>(plan);
+    const double m = (double)P->W * (double)P->n;
+    const double L = I0 * normA_sq / m * P->Csum_mu;
+    *eta = 1.0 / (4.0 * L);
+    return EXACT_OK;
+}
+
+exact_status exact_plan_nnz(exact_plan_t plan, long long *nnz)
+{
+    if (!plan || !nnz) return EXACT_ERR_INVALID_ARG;
+    Plan *P = reinterpret_cast<Plan *>(plan);
+    if (P->nnz == 0) P->nnz = count_nnz(P->g);
+    *nnz = P->nnz;
+    return EXACT_OK;
+}
+
+exact_status exact_profile_enable(exact_plan_t plan, int sample_every)
+{
+    exact_status st = check_plan(plan, false);
+    if (st != EXACT_OK) return st;
+    if (sample_every < 0) return EXACT_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    if (sample_every > 0 && !P.prof_ev) {
+        const int cap = 4096;
+        P.prof_ev = new (std::nothrow) cudaEvent_t[2 * cap];
+        P.prof_kind = new (std::nothrow) int[cap];
+        if (!P.prof_ev || !P.prof_kind) {
+            delete[] P.prof_ev;
+            delete[] P.prof_kind;
+            P.prof_ev = nullptr;
+            P.prof_kind = nullptr;
+            return EXACT_ERR_OOM;
+        }
+        for (int i = 0; i < 2 * cap; ++i) {
+            if (cudaEventCreate(&P.prof_ev[i]) != cudaSuccess) {
+                P.prof_cap = i / 2;
+                prof_free(P);
+                return EXACT_ERR_OOM;
+            }
+        }
+        P.prof_cap = cap;
+        P.prof_used = 0;
+    }
+    P.prof_every = sample_every;
+    return EXACT_OK;
+}
+
+exact_status exact_profile_read(exact_plan_t plan, double *ms, long long *launches)
+{
+    exact_status st = check_plan(plan, false);
+    if (st != EXACT_OK) return st;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    double acc[EXACT_PROF_KINDS] = {0.0};
+    long long cnt[EXACT_PROF_KINDS] = {0};
+    for (int u = 0; u < P.prof_used; ++u) {
+        float t = 0.0f;
+        EXACT_TRY(cudaEventSynchronize(P.prof_ev[2 * u + 1]));
+        EXACT_TRY(cudaEventElapsedTime(&t, P.prof_ev[2 * u], P.prof_ev[2 * u + 1]));
+        acc[P.prof_kind[u]] += t;
+        cnt[P.prof_kind[u]] += 1;
+    }
+    P.prof_used = 0;
+    for (int k = 0; k < EXACT_PROF_KINDS; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (launches) launches[k] = cnt[k];
+    }
+    return EXACT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+// exact_internal.h -- types shared by the host plan code and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/exact.h"
+
+namespace exact {
+
+// Zero columns kept on each side of a padded image row so that a Joseph sample
+// at cross index k0 in [-2, n_cross] can read k0 and k0+1 without a bounds test.
+constexpr int kPad = 2;
+constexpr int kMaxK = EXACT_MAX_ENERGY;
+
+// One ray of the Joseph projector (FP32 copy).  Cross-axis index coordinate at
+// driving index j is t = fmaf(beta, j, alpha); A entries are delta*(1-|t-k|)_+.
+// bits: 0-14 first driving index j_lo, 15-29 last j_hi, 30 driving axis
+// (0: x drives, image read through the column-major copy; 1: y drives).
+struct __align__(16) RayF {
+    float alpha, beta, delta;
+    int bits;
+};
+
+struct __align__(16) RayD {
+    double alpha, beta, delta;
+    int bits, pad;
+};
+
+__host__ __device__ inline int ray_jlo(int bits) { return bits & 0x7fff; }
+__host__ __device__ inline int ray_jhi(int bits) { return (bits >> 15) & 0x7fff; }
+__host__ __device__ inline int ray_axis(int bits) { return (bits >> 30) & 1; }
+
+// Per-view back-projection table.  The continuous bin coordinate of the point
+// at pixel-index position (kx, ky) is (n0 + n1 kx + n2 ky) / (d0 + d1 kx + d2 ky) + c
+// (parallel beam: d0 = 1, d1 = d2 = 0).  flags bit 0: the view has x-driven
+// rays, bit 1: y-driven rays.
+struct __align__(16) ViewRec {
+    float n0, n1, n2, c;
+    float d0, d1, d2;
+    int flags;
+};
+
+// Device-side status words of a solve or a norm estimate.
+struct DevState {
+    int done;         // nonzero: later kernels of this solve return at once
+    int iters_done;
+    int status;       // exact_status
+    int pad;
+    double rel_res;
+    double lam;       // power iteration: latest ||A v||^2
+    double lam_prev;
+    double inv_norm;  // power iteration: 1/||w|| for the next forward
+};
+
+struct Plan {
+    exact_geometry g;
+    int device = -1;
+    int W = 0, K = 0;
+    long long n = 0, d = 0;
+    double Csum_mu = 0.0;          // sum_k mu_k sum_w S[w][k]
+    float mu_log2e[kMaxK];         // mu_k * log2(e), FP32
+    float C[kMaxK];                // sum_w S[w][k], FP32 (multiplied by I0 per call)
+    RayF *rays_f = nullptr;        // [n]
+    RayD *rays_d = nullptr;        // [n]
+    ViewRec *views = nullptr;      // [n_views]
+    // workspace carve-up (all device pointers inside the bound workspace)
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    float *xr[2] = {nullptr, nullptr};   // padded row-major copies   [ny][nx + 2 kPad]
+    float *xc[2] = {nullptr, nullptr};   // padded column-major copies [nx][ny + 2 kPad]
+    float *Y = nullptr;                  // collapsed counts [n]
+    float *r = nullptr;                  // residual [n]
+    double *partials = nullptr;          // per-block FP64 partial sums
+    double *avg = nullptr;               // tail-average accumulator [d]
+    double *xrd = nullptr, *xcd = nullptr;  // FP64 padded copies (power iteration)
+    double *zd = nullptr;                // FP64 projections [n]
+    DevState *state = nullptr;
+    // pinned host mirror of the device state (solve info)
+    DevState *host_state = nullptr;
+    long long nnz = 0;              // nonzero entries of A
+    // kernel timing (profiling aid): event pairs recorded around sampled launches
+    int prof_every = 0;
+    int prof_used = 0;              // event pairs recorded since the last read
+    int prof_cap = 0;
+    cudaEvent_t *prof_ev = nullptr; // [2 * prof_cap]
+    int *prof_kind = nullptr;       // [prof_cap]
+    long long ldr() const { return g.nx + 2 * kPad; }
+    long long ldc() const { return g.ny + 2 * kPad; }
+};
+
+// ---- launch parameter blocks -------------------------------------------------
+
+struct ImgF {
+    const float *xr;  // padded row-major (read by y-driven rays)
+    const float *xc;  // padded column-major (read by x-driven rays)
+    int nx, ny;
+    long long ldr, ldc;
+};
+
+struct FwdArgs {
+    ImgF img;
+    const RayF *rays;
+    long long n;
+    float *z;             // z output (link == false)
+    const float *Y;       // collapsed counts (link == true)
+    float *r;             // residual output (link == true)
+    int K;
+    const DevState *state;  // may be null: if set and state->done, return
+};
+
+// Link coefficients passed by value (kernel parameter space).
+struct LinkCoef {
+    float mu2[kMaxK];  // mu_k log2(e)
+    float c[kMaxK];    // I0 sum_w S[w][k]
+};
+
+enum AdjMode { ADJ_PLAIN = 0, ADJ_EG = 1, ADJ_EG_FINAL = 2 };
+
+struct AdjArgs {
+    const RayF *rays;
+    const ViewRec *views;
+    int n_views, n_bins, nx, ny;
+    const float *r;        // [n] residual (multiplied by each ray's delta on the fly)
+    float scale;           // out = scale * A^T r   (PLAIN)  |  x_base + scale * A^T r (EG)
+    float *out;            // PLAIN: [ny][nx] output
+    const float *base_r;   // EG: padded row-major base iterate x_t
+    float *out_r;          // EG: padded row-major output
+    float *out_c;          // EG: padded column-major output
+    long long ldr, ldc;
+    float lo, hi;
+    double *partials;      // EG_FINAL: per-block (||x_out - x_base||^2, ||x_base||^2)
+    double *avg;           // EG_FINAL: tail-average accumulator or null
+    int avg_from;          // EG_FINAL: accumulate when iteration index >= avg_from
+    int iter;              // iteration index of this launch
+    const DevState *state;
+};
+
+// ---- launchers (each returns cudaGetLastError()) ------------------------------
+cudaError_t launch_forward(const FwdArgs &a, bool link, const LinkCoef *coef, cudaStream_t s);
+cudaError_t launch_adjoint(const AdjArgs &a, int mode, bool fan, cudaStream_t s);
+int adjoint_blocks(int nx, int ny);
+
+cudaError_t launch_pack(const float *x, float *xr, float *xc, int nx, int ny, long long ldr, long long ldc,
+                        float lo, float hi, bool project, cudaStream_t s);
+cudaError_t launch_unpack(const float *xr, long long ldr, int nx, int ny, float *x, const double *avg,
+                          const DevState *state, int avg_from, cudaStream_t s);
+cudaError_t launch_collapse(const void *y, int dtype, int W, long long n, float *Y, cudaStream_t s);
+cudaError_t launch_solve_reduce(const double *partials, int nparts, DevState *st, int iter, double tol,
+                                int check_every, cudaStream_t s);
+cudaError_t launch_reset_state(DevState *st, cudaStream_t s);
+
+// FP64 power iteration pieces
+cudaError_t launch_power_init(double *xrd, double *xcd, int nx, int ny, long long ldr, long long ldc,
+                              DevState *st, cudaStream_t s);
+cudaError_t launch_forward_d(const RayD *rays, long long n, const double *xrd, const double *xcd, int nx,
+                             int ny, long long ldr, long long ldc, double *zd, double *partials,
+                             DevState *st, cudaStream_t s);
+int forward_d_blocks(long long n);
+cudaError_t launch_adjoint_d(const RayD *rays, const ViewRec *views, int n_views, int n_bins, int nx, int ny,
+                             const double *zd, double *xrd, double *xcd, long long ldr, long long ldc,
+                             double *partials, DevState *st, bool fan, cudaStream_t s);
+cudaError_t launch_power_reduce(const double *pz, int nz, const double *pw, int nw, DevState *st, int iter,
+                                double rtol, cudaStream_t s);
+
+}  // namespace exact

@@ -1,0 +1,250 @@
+// k_util.cu -- small kernels around the hot path: image packing into the
+// padded row- and column-major copies, the window sum of the counts, the
+// fixed-order FP64 reductions that drive stopping (solve) and convergence
+// (power iteration), and state resets.  None of these loops over rays.
+#include "exact_internal.h"
+
+#include <math.h>
+
+namespace exact {
+
+namespace {
+
+__device__ __forceinline__ float proj(float v, float lo, float hi, bool project)
+{
+    return project ? (v < lo ? lo : (v > hi ? hi : v)) : v;
+}
+
+// Row-major copy with kPad zero columns on each side.
+__global__ void k_pack_rows(const float *x, float *xr, int nx, int ny, long long ldr, float lo, float hi,
+                            bool project)
+{
+    const long long total = (long long)ny * ldr;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long j = e / ldr;
+        const long long k = e - j * ldr - kPad;
+        xr[e] = (k >= 0 && k < nx) ? proj(x[j * nx + k], lo, hi, project) : 0.0f;
+    }
+}
+
+// Column-major copy (x transposed) with kPad zero entries on each side,
+// through a shared-memory tile.
+__global__ void k_pack_cols(const float *x, float *xc, int nx, int ny, long long ldc, float lo, float hi,
+                            bool project)
+{
+    __shared__ float tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int iy = by + r, ix = bx + threadIdx.x;
+        tile[r][threadIdx.x] = (ix < nx && iy < ny) ? proj(x[(long long)iy * nx + ix], lo, hi, project) : 0.0f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int ix = bx + r, iy = by + threadIdx.x;
+        if (ix < nx && iy < ny) xc[(long long)ix * ldc + iy + kPad] = tile[threadIdx.x][r];
+    }
+    // pads of the rows this block owns
+    if (blockIdx.y == 0 && threadIdx.y == 0 && threadIdx.x < 32) {
+        const int ix = bx + threadIdx.x;
+        if (ix < nx) {
+            for (int p = 0; p < kPad; ++p) {
+                xc[(long long)ix * ldc + p] = 0.0f;
+                xc[(long long)ix * ldc + kPad + ny + p] = 0.0f;
+            }
+        }
+    }
+}
+
+__global__ void k_unpack(const float *xr, long long ldr, int nx, int ny, float *x, const double *avg,
+                         const DevState *st, int avg_from)
+{
+    const long long d = (long long)nx * ny;
+    long long cnt = 0;
+    if (avg) cnt = (long long)st->iters_done - avg_from;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < d;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long j = p / nx, k = p - j * nx;
+        if (avg && cnt > 0)
+            x[p] = (float)(avg[p] / (double)cnt);
+        else
+            x[p] = xr[j * ldr + k + kPad];
+    }
+}
+
+template <typename Tin>
+__device__ __forceinline__ float to_f(Tin v);
+template <>
+__device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename Tin>
+__global__ void k_collapse(const Tin *y, int W, long long n, float *Y)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int w = 0; w < W; ++w) s += to_f<Tin>(y[(long long)w * n + i]);
+        Y[i] = s;
+    }
+}
+
+constexpr int RT = 256;  // threads of the single-block reductions
+
+// Fixed-order sum over `count` values with stride `stride` starting at `src`,
+// result in thread 0.
+__device__ double block_sum_fixed(const double *src, int count, int stride)
+{
+    __shared__ double s[RT];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < count; i += RT) acc += src[(long long)i * stride];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = RT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = s[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(RT) k_solve_reduce(const double *partials, int nparts, DevState *st, int iter,
+                                                     double tol, int check_every)
+{
+    if (st->done) return;
+    const double num = block_sum_fixed(partials, nparts, 2);
+    const double den = block_sum_fixed(partials + 1, nparts, 2);
+    if (threadIdx.x == 0) {
+        const double rel = sqrt(num) / fmax(sqrt(den), 1e-30);
+        st->rel_res = rel;
+        st->iters_done = iter + 1;
+        if (!isfinite(rel)) {
+            st->status = EXACT_ERR_NONFINITE;
+            st->done = 1;
+        } else if (tol > 0.0 && check_every > 0 && (iter + 1) % check_every == 0 && rel <= tol) {
+            st->done = 1;
+        }
+    }
+}
+
+__global__ void k_reset_state(DevState *st)
+{
+    st->done = 0;
+    st->iters_done = 0;
+    st->status = EXACT_OK;
+    st->rel_res = 0.0;
+    st->lam = 0.0;
+    st->lam_prev = 0.0;
+    st->inv_norm = 1.0;
+}
+
+__global__ void k_power_init(double *xrd, double *xcd, int nx, int ny, long long ldr, long long ldc, DevState *st)
+{
+    const long long tr = (long long)ny * ldr, tc = (long long)nx * ldc;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tr + tc;
+         e += (long long)gridDim.x * blockDim.x) {
+        if (e < tr) {
+            const long long k = e % ldr - kPad;
+            xrd[e] = (k >= 0 && k < nx) ? 1.0 : 0.0;
+        } else {
+            const long long k = (e - tr) % ldc - kPad;
+            xcd[e - tr] = (k >= 0 && k < ny) ? 1.0 : 0.0;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->done = 0;
+        st->iters_done = 0;
+        st->status = EXACT_OK;
+        st->lam = 0.0;
+        st->lam_prev = 0.0;
+        st->inv_norm = 1.0 / sqrt((double)nx * (double)ny);
+    }
+}
+
+__global__ void __launch_bounds__(RT) k_power_reduce(const double *pz, int nz, const double *pw, int nw,
+                                                     DevState *st, int iter, double rtol)
+{
+    if (st->done) return;
+    const double lam = block_sum_fixed(pz, nz, 1);
+    const double w2 = block_sum_fixed(pw, nw, 1);
+    if (threadIdx.x == 0) {
+        st->lam = lam;
+        st->iters_done = iter + 1;
+        const double nrm = sqrt(w2);
+        if (!(nrm > 0.0) || !isfinite(nrm)) {
+            if (!isfinite(nrm)) st->status = EXACT_ERR_NONFINITE;
+            st->done = 1;
+        } else {
+            st->inv_norm = 1.0 / nrm;
+            if (iter > 0 && rtol > 0.0 && fabs(lam - st->lam_prev) <= rtol * lam) st->done = 1;
+            st->lam_prev = lam;
+        }
+    }
+}
+
+unsigned grid_for(long long work, int threads)
+{
+    long long b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const float *x, float *xr, float *xc, int nx, int ny, long long ldr, long long ldc,
+                        float lo, float hi, bool project, cudaStream_t s)
+{
+    k_pack_rows<<<grid_for((long long)ny * ldr, 256), 256, 0, s>>>(x, xr, nx, ny, ldr, lo, hi, project);
+    const dim3 grid((nx + 31) / 32, (ny + 31) / 32);
+    k_pack_cols<<<grid, dim3(32, 8), 0, s>>>(x, xc, nx, ny, ldc, lo, hi, project);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(const float *xr, long long ldr, int nx, int ny, float *x, const double *avg,
+                          const DevState *state, int avg_from, cudaStream_t s)
+{
+    k_unpack<<<grid_for((long long)nx * ny, 256), 256, 0, s>>>(xr, ldr, nx, ny, x, avg, state, avg_from);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collapse(const void *y, int dtype, int W, long long n, float *Y, cudaStream_t s)
+{
+    if (dtype == EXACT_BF16)
+        k_collapse<__nv_bfloat16><<<grid_for(n, 256), 256, 0, s>>>((const __nv_bfloat16 *)y, W, n, Y);
+    else
+        k_collapse<float><<<grid_for(n, 256), 256, 0, s>>>((const float *)y, W, n, Y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_reduce(const double *partials, int nparts, DevState *st, int iter, double tol,
+                                int check_every, cudaStream_t s)
+{
+    k_solve_reduce<<<1, RT, 0, s>>>(partials, nparts, st, iter, tol, check_every);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_state(DevState *st, cudaStream_t s)
+{
+    k_reset_state<<<1, 1, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_power_init(double *xrd, double *xcd, int nx, int ny, long long ldr, long long ldc,
+                              DevState *st, cudaStream_t s)
+{
+    k_power_init<<<grid_for((long long)ny * ldr + (long long)nx * ldc, 256), 256, 0, s>>>(xrd, xcd, nx, ny, ldr,
+                                                                                        ldc, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_power_reduce(const double *pz, int nz, const double *pw, int nw, DevState *st, int iter,
+                                double rtol, cudaStream_t s)
+{
+    k_power_reduce<<<1, RT, 0, s>>>(pz, nz, pw, nw, st, iter, rtol);
+    return cudaGetLastError();
+}
+
+}  // namespace exact

@@ -1,0 +1,303 @@
+"""Thin Python binding of ``libexact.so`` (include/exact.h).
+
+Argument marshalling only: tensors are checked (device, dtype, shape,
+contiguity) and passed as raw pointers with the current torch stream; every
+step of the computation runs in the library's CUDA kernels.  Loading fails
+loudly when the library cannot be built or loaded; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+EXACT_OK = 0
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "timeout",
+          5: "non-finite residual", 6: "unsupported", 7: "no workspace bound"}
+F32, BF16 = 0, 1
+MAX_ENERGY = 256
+
+
+class ExactError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn} failed: {STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+class _Geometry(ctypes.Structure):
+    _fields_ = [("beam", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("pixel", ctypes.c_double), ("n_views", ctypes.c_int),
+                ("angle0", ctypes.c_double), ("angle_range", ctypes.c_double),
+                ("n_bins", ctypes.c_int), ("bin_pitch", ctypes.c_double),
+                ("det_offset", ctypes.c_double), ("src_to_center", ctypes.c_double),
+                ("src_to_det", ctypes.c_double)]
+
+
+class _Spectrum(ctypes.Structure):
+    _fields_ = [("n_energy", ctypes.c_int), ("mu", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Windows(ctypes.Structure):
+    _fields_ = [("n_windows", ctypes.c_int), ("S", ctypes.POINTER(ctypes.c_double))]
+
+
+class _SolveOpts(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double), ("hi", ctypes.c_double), ("tol", ctypes.c_double),
+                ("check_every", ctypes.c_int), ("average_tail", ctypes.c_int)]
+
+
+class _SolveInfo(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int), ("rel_res", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+_lib = None
+
+# every function declared in include/exact.h: (name, restype, argtypes)
+_VP, _CP = ctypes.c_void_p, ctypes.c_char_p
+_SIGS = [
+    ("exact_plan_create", ctypes.c_int, [ctypes.POINTER(_Geometry), ctypes.POINTER(_Spectrum),
+                                         ctypes.POINTER(_Windows), ctypes.POINTER(_VP)]),
+    ("exact_plan_destroy", ctypes.c_int, [_VP]),
+    ("exact_plan_dims", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    ("exact_plan_workspace_bytes", ctypes.c_size_t, [_VP]),
+    ("exact_plan_bind_workspace", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    ("exact_forward", ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    ("exact_adjoint", ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    ("exact_operator", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP, _VP]),
+    ("exact_solve_opts_default", _SolveOpts, []),
+    ("exact_solve", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                   ctypes.POINTER(_SolveOpts), _VP, ctypes.POINTER(_SolveInfo), _VP]),
+    ("exact_norm_estimate", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_int), _VP]),
+    ("exact_recommended_eta", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_double)]),
+    ("exact_plan_nnz", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    ("exact_profile_enable", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("exact_profile_read", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    ("exact_status_string", _CP, [ctypes.c_int]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Load libexact.so (building it first if missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_needed else _build.LIB
+        lib = ctypes.CDLL(path)
+        for name, res, args in _SIGS:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(fn: str, status: int):
+    if status != EXACT_OK:
+        raise ExactError(fn, status)
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass(frozen=True)
+class Geometry:
+    """Scan geometry, same fields and meaning as ``exact_geometry``."""
+    beam: int
+    nx: int
+    ny: int
+    n_views: int
+    n_bins: int
+    pixel: float = 1.0
+    angle0: float = 0.0
+    angle_range: float = math.pi
+    bin_pitch: float = 1.0
+    det_offset: float = 0.0
+    src_to_center: float = 0.0
+    src_to_det: float = 0.0
+
+    @property
+    def n_rays(self) -> int:
+        return self.n_views * self.n_bins
+
+    def _c(self) -> _Geometry:
+        return _Geometry(self.beam, self.nx, self.ny, self.pixel, self.n_views, self.angle0,
+                         self.angle_range, self.n_bins, self.bin_pitch, self.det_offset,
+                         self.src_to_center, self.src_to_det)
+
+
+@dataclass
+class SolveInfo:
+    iters_done: int
+    rel_res: float
+    status: int
+
+
+class Plan:
+    """An EXACT plan on the current CUDA device, with its workspace.
+
+    ``mu``: attenuation per energy bin (K values > 0); ``S``: window weights
+    [W][K] >= 0 (fraction of I0 recorded by window w from energy k)."""
+
+    def __init__(self, geometry: Geometry, mu, S, device=None):
+        lib = load()
+        self.geometry = geometry
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        mu_l = [float(v) for v in mu]
+        S_rows = [[float(v) for v in row] for row in S]
+        self.K, self.W = len(mu_l), len(S_rows)
+        if any(len(r) != self.K for r in S_rows):
+            raise ValueError("S must be [n_windows][n_energy]")
+        self._mu = (ctypes.c_double * self.K)(*mu_l)
+        self._S = (ctypes.c_double * (self.K * self.W))(*[v for r in S_rows for v in r])
+        g = geometry._c()
+        sp = _Spectrum(self.K, ctypes.cast(self._mu, ctypes.POINTER(ctypes.c_double)))
+        wn = _Windows(self.W, ctypes.cast(self._S, ctypes.POINTER(ctypes.c_double)))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check("exact_plan_create", lib.exact_plan_create(ctypes.byref(g), ctypes.byref(sp),
+                                                              ctypes.byref(wn), ctypes.byref(h)))
+            self._h = h
+            nbytes = int(lib.exact_plan_workspace_bytes(h))
+            # over-allocate so the start can be rounded up to 256 bytes
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            off = (-self._ws.data_ptr()) % 256
+            _check("exact_plan_bind_workspace",
+                   lib.exact_plan_bind_workspace(h, ctypes.c_void_p(self._ws.data_ptr() + off), nbytes))
+        self.n_rays = geometry.n_views * geometry.n_bins
+        self.shape_img = (geometry.ny, geometry.nx)
+        self.shape_sino = (geometry.n_views, geometry.n_bins)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            with torch.cuda.device(self.device):
+                torch.cuda.synchronize(self.device)
+                load().exact_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- argument checks ----------------------------------------------------
+    def _t(self, t: torch.Tensor, shape, dtypes=(torch.float32,), name="tensor") -> torch.Tensor:
+        if not isinstance(t, torch.Tensor) or t.device != self.device:
+            raise ValueError(f"{name} must be a tensor on {self.device}")
+        if t.dtype not in dtypes:
+            raise ValueError(f"{name} must have dtype in {dtypes}, got {t.dtype}")
+        if tuple(t.shape) != tuple(shape) and t.numel() != math.prod(shape):
+            raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        return t
+
+    def _y(self, y: torch.Tensor):
+        self._t(y, (self.W,) + self.shape_sino, (torch.float32, torch.bfloat16), "y")
+        return F32 if y.dtype == torch.float32 else BF16
+
+    # ---- entry points -------------------------------------------------------
+    def forward(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        self._t(x, self.shape_img, name="x")
+        z = out if out is not None else torch.empty(self.shape_sino, dtype=torch.float32, device=self.device)
+        self._t(z, self.shape_sino, name="z")
+        _check("exact_forward", load().exact_forward(self._h, _ptr(x), _ptr(z), _stream()))
+        return z
+
+    def adjoint(self, r: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        self._t(r, self.shape_sino, name="r")
+        g = out if out is not None else torch.empty(self.shape_img, dtype=torch.float32, device=self.device)
+        self._t(g, self.shape_img, name="g")
+        _check("exact_adjoint", load().exact_adjoint(self._h, _ptr(r), _ptr(g), _stream()))
+        return g
+
+    def operator(self, x: torch.Tensor, y: torch.Tensor, I0: float, out: torch.Tensor | None = None):
+        self._t(x, self.shape_img, name="x")
+        dt = self._y(y)
+        F = out if out is not None else torch.empty(self.shape_img, dtype=torch.float32, device=self.device)
+        self._t(F, self.shape_img, name="F")
+        _check("exact_operator", load().exact_operator(self._h, _ptr(x), _ptr(y), dt, float(I0), _ptr(F),
+                                                       _stream()))
+        return F
+
+    def solve(self, y: torch.Tensor, I0: float, eta: float, iters: int, x: torch.Tensor | None = None,
+              lo: float = 0.0, hi: float = math.inf, tol: float = 0.0, check_every: int = 1,
+              average_tail: bool = False, sync: bool = True):
+        """Run ``iters`` extragradient iterations in place on ``x`` (zeros if
+        None).  Returns (x, SolveInfo); with sync=False the info is filled
+        once the current stream reaches the end of the solve."""
+        dt = self._y(y)
+        if x is None:
+            x = torch.zeros(self.shape_img, dtype=torch.float32, device=self.device)
+        self._t(x, self.shape_img, name="x")
+        opts = _SolveOpts(float(lo), float(hi), float(tol), int(check_every), int(bool(average_tail)))
+        info = _SolveInfo()
+        self._info = info  # keep alive until the host callback has run
+        _check("exact_solve", load().exact_solve(self._h, _ptr(y), dt, float(I0), float(eta), int(iters),
+                                                 ctypes.byref(opts), _ptr(x), ctypes.byref(info), _stream()))
+        if sync:
+            torch.cuda.current_stream().synchronize()
+        return x, info
+
+    def norm_estimate(self, max_iters: int = 500, rtol: float = 1e-9):
+        """FP64 power-iteration estimate of ||A||^2 (synchronises); returns (lam, iterations)."""
+        lam = ctypes.c_double()
+        it = ctypes.c_int()
+        _check("exact_norm_estimate", load().exact_norm_estimate(self._h, int(max_iters), float(rtol),
+                                                                 ctypes.byref(lam), ctypes.byref(it), _stream()))
+        return lam.value, it.value
+
+    def nnz(self) -> int:
+        """Nonzero entries of A (counted on the host, cached)."""
+        v = ctypes.c_longlong()
+        _check("exact_plan_nnz", load().exact_plan_nnz(self._h, ctypes.byref(v)))
+        return v.value
+
+    def profile_enable(self, sample_every: int):
+        _check("exact_profile_enable", load().exact_profile_enable(self._h, int(sample_every)))
+
+    def profile_read(self):
+        """{kind: (total ms, launches)} for kinds forward_link, adjoint_half,
+        adjoint_full, reduce, since the last read."""
+        ms = (ctypes.c_double * 4)()
+        cnt = (ctypes.c_longlong * 4)()
+        _check("exact_profile_read", load().exact_profile_read(self._h, ms, cnt))
+        names = ("forward_link", "adjoint_half", "adjoint_full", "reduce")
+        return {n: (ms[i], cnt[i]) for i, n in enumerate(names)}
+
+    def solve_host(self, y_host: torch.Tensor, I0: float, eta: float, iters: int, x_host: torch.Tensor,
+                   y_dev: torch.Tensor | None = None, x_dev: torch.Tensor | None = None, **opts):
+        """Solve from host buffers: copy y and x_1 from (pinned) host memory,
+        solve on the device, copy the result back into ``x_host``.  All copies
+        are enqueued on the current stream; returns (x_host, SolveInfo) after
+        synchronising."""
+        if y_dev is None:
+            y_dev = torch.empty(y_host.shape, dtype=y_host.dtype, device=self.device)
+        if x_dev is None:
+            x_dev = torch.empty(x_host.shape, dtype=x_host.dtype, device=self.device)
+        y_dev.copy_(y_host, non_blocking=True)
+        x_dev.copy_(x_host, non_blocking=True)
+        _, info = self.solve(y_dev, I0, eta, iters, x=x_dev, sync=False, **opts)
+        x_host.copy_(x_dev, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return x_host, info
+
+    def recommended_eta(self, I0: float, normA_sq: float) -> float:
+        eta = ctypes.c_double()
+        _check("exact_recommended_eta", load().exact_recommended_eta(self._h, float(I0), float(normA_sq),
+                                                                     ctypes.byref(eta)))
+        return eta.value

@@ -1,0 +1,71 @@
+"""The C-ABI library builds, loads without a GPU, and exports every function
+include/exact.h declares; the Python binding's struct layouts match the C
+ones (checked with gcc's offsetof)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "exact.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*[a-z_][a-z_ *]*?\b(exact_[a-z_0-9]+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("exact_plan_create", "exact_forward", "exact_adjoint", "exact_operator", "exact_solve",
+                     "exact_norm_estimate", "exact_plan_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2503_19925_gb300 as ex
+    lib = ex.load()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    from paper_2503_19925_gb300.exact import _SIGS
+    bound = {n for n, _, _ in _SIGS}
+    assert set(declared_functions()) <= bound
+    assert lib.exact_status_string(0) == b"ok"
+
+
+def test_struct_layouts_match(tmp_path):
+    from paper_2503_19925_gb300 import exact as b
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "exact.h"\n'
+                   'int main(void){\n'
+                   'printf("%zu %zu %zu %zu\\n", sizeof(exact_geometry), offsetof(exact_geometry, pixel),'
+                   ' offsetof(exact_geometry, n_bins), offsetof(exact_geometry, src_to_det));\n'
+                   'printf("%zu %zu\\n", sizeof(exact_solve_opts), offsetof(exact_solve_opts, average_tail));\n'
+                   'printf("%zu %zu\\n", sizeof(exact_solve_info), offsetof(exact_solve_info, status));\n'
+                   'printf("%zu %zu\\n", sizeof(exact_spectrum), sizeof(exact_windows));\n'
+                   'return 0;}\n')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    g = [int(v) for v in out[0].split()]
+    assert g == [ctypes.sizeof(b._Geometry), b._Geometry.pixel.offset, b._Geometry.n_bins.offset,
+                 b._Geometry.src_to_det.offset]
+    o = [int(v) for v in out[1].split()]
+    assert o == [ctypes.sizeof(b._SolveOpts), b._SolveOpts.average_tail.offset]
+    i = [int(v) for v in out[2].split()]
+    assert i == [ctypes.sizeof(b._SolveInfo), b._SolveInfo.status.offset]
+    s = [int(v) for v in out[3].split()]
+    assert s == [ctypes.sizeof(b._Spectrum), ctypes.sizeof(b._Windows)]
+
+
+def test_product_path_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2503_19925_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".h", ".cuh", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "exact_oracle" not in text and "liboracle" not in text, f
