@@ -129,7 +129,7 @@ RayHost make_ray(const exact_geometry &g, int v, int b)
     return r;
 }
 
-ViewRec make_view(const exact_geometry &g, int v, int flags)
+ViewRec make_view(const exact_geometry &g, int v, int xb0, int xb1, int yb0, int yb1)
 {
     const double th = g.angle0 + (double)v * g.angle_range / (double)g.n_views;
     const double c = cos(th), s = sin(th), p = g.pixel;
@@ -155,7 +155,11 @@ ViewRec make_view(const exact_geometry &g, int v, int flags)
         r.d2 = (float)(-s * p);
     }
     r.c = (float)cc;
-    r.flags = flags;
+    r.pad = 0.0f;
+    r.xb0 = xb0;
+    r.xb1 = xb1;
+    r.yb0 = yb0;
+    r.yb1 = yb1;
     return r;
 }
 
@@ -354,31 +358,60 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
 
     const exact_geometry &g = *geometry;
     std::vector<RayF> rf((size_t)P->n);
+    std::vector<int> rbits((size_t)P->n);
+    std::vector<float> rdelta((size_t)P->n);
     std::vector<RayD> rd((size_t)P->n);
     std::vector<ViewRec> vw((size_t)g.n_views);
     for (int v = 0; v < g.n_views; ++v) {
-        int flags = 0;
+        int switches = 0;
+        int prev_axis = -1;
+        int first_axis = -1, sw = g.n_bins;
         for (int b = 0; b < g.n_bins; ++b) {
             const RayHost h = make_ray(g, v, b);
             const int bits = (h.jlo & 0x7fff) | ((h.jhi & 0x7fff) << 15) | (h.axis << 30);
             const size_t i = (size_t)v * g.n_bins + b;
-            rf[i].alpha = (float)h.alpha;
-            rf[i].beta = (float)h.beta;
-            rf[i].delta = (float)h.delta;
-            rf[i].bits = bits;
+            const double A = floor(h.alpha);
+            const float bh = (float)h.beta;
+            rf[i].A = (float)A;
+            rf[i].a = (float)(h.alpha - A);
+            rf[i].bh = bh;
+            rf[i].bl = (float)(h.beta - (double)bh);
+            rbits[i] = bits;
+            rdelta[i] = (float)h.delta;
             rd[i].alpha = h.alpha;
             rd[i].beta = h.beta;
             rd[i].delta = h.delta;
             rd[i].bits = bits;
             rd[i].pad = 0;
-            flags |= h.axis ? 2 : 1;
+            if (b == 0) first_axis = h.axis;
+            if (prev_axis >= 0 && h.axis != prev_axis) {
+                ++switches;
+                sw = b;
+            }
+            prev_axis = h.axis;
         }
-        vw[v] = make_view(g, v, flags);
+        if (switches > 1) {  // driving axis must switch at most once per view (fan angle below 90 degrees)
+            delete P;
+            return EXACT_ERR_UNSUPPORTED;
+        }
+        // segment [0, sw) has first_axis, [sw, n_bins) the other one
+        int xb0 = 0, xb1 = 0, yb0 = 0, yb1 = 0;
+        if (first_axis == 0) {
+            xb0 = 0; xb1 = sw; yb0 = sw; yb1 = g.n_bins;
+        } else {
+            yb0 = 0; yb1 = sw; xb0 = sw; xb1 = g.n_bins;
+        }
+        vw[v] = make_view(g, v, xb0, xb1, yb0, yb1);
     }
     cudaError_t e = cudaMalloc(&P->rays_f, sizeof(RayF) * rf.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->ray_bits, sizeof(int) * rbits.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->ray_delta, sizeof(float) * rdelta.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->rays_d, sizeof(RayD) * rd.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->views, sizeof(ViewRec) * vw.size());
     if (e == cudaSuccess) e = cudaMemcpy(P->rays_f, rf.data(), sizeof(RayF) * rf.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->ray_bits, rbits.data(), sizeof(int) * rbits.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(P->ray_delta, rdelta.data(), sizeof(float) * rdelta.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->rays_d, rd.data(), sizeof(RayD) * rd.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->views, vw.data(), sizeof(ViewRec) * vw.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMallocHost(&P->host_state, sizeof(DevState));
@@ -399,6 +432,8 @@ exact_status exact_plan_destroy(exact_plan_t plan)
     cudaGetDevice(&prev);
     if (P->device >= 0 && prev != P->device) cudaSetDevice(P->device);
     if (P->rays_f) cudaFree(P->rays_f);
+    if (P->ray_bits) cudaFree(P->ray_bits);
+    if (P->ray_delta) cudaFree(P->ray_delta);
     if (P->rays_d) cudaFree(P->rays_d);
     if (P->views) cudaFree(P->views);
     if (P->host_state) cudaFreeHost(P->host_state);
@@ -459,6 +494,8 @@ exact_status exact_forward(exact_plan_t plan, const float *x, float *z, exact_st
     memset(&a, 0, sizeof(a));
     a.img = img_of(P, 0);
     a.rays = P.rays_f;
+    a.bits = P.ray_bits;
+    a.delta = P.ray_delta;
     a.n = P.n;
     a.z = z;
     EXACT_TRY(launch_forward(a, false, nullptr, s));
@@ -480,6 +517,7 @@ exact_status exact_adjoint(exact_plan_t plan, const float *r, float *g, exact_st
     a.nx = P.g.nx;
     a.ny = P.g.ny;
     a.r = r;
+    a.delta = P.ray_delta;
     a.scale = 1.0f;
     a.out = g;
     EXACT_TRY(launch_adjoint(a, ADJ_PLAIN, P.g.beam == 1, reinterpret_cast<cudaStream_t>(stream)));
@@ -503,6 +541,8 @@ exact_status exact_operator(exact_plan_t plan, const float *x, const void *y, ex
     memset(&f, 0, sizeof(f));
     f.img = img_of(P, 0);
     f.rays = P.rays_f;
+    f.bits = P.ray_bits;
+    f.delta = P.ray_delta;
     f.n = P.n;
     f.Y = P.Y;
     f.r = P.r;
@@ -552,6 +592,8 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     FwdArgs f;
     memset(&f, 0, sizeof(f));
     f.rays = P.rays_f;
+    f.bits = P.ray_bits;
+    f.delta = P.ray_delta;
     f.n = P.n;
     f.Y = P.Y;
     f.r = P.r;

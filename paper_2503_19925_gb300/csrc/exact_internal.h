@@ -14,32 +14,40 @@ namespace exact {
 constexpr int kPad = 2;
 constexpr int kMaxK = EXACT_MAX_ENERGY;
 
-// One ray of the Joseph projector (FP32 copy).  Cross-axis index coordinate at
-// driving index j is t = fmaf(beta, j, alpha); A entries are delta*(1-|t-k|)_+.
-// bits: 0-14 first driving index j_lo, 15-29 last j_hi, 30 driving axis
-// (0: x drives, image read through the column-major copy; 1: y drives).
+// One ray of the Joseph projector, FP32 form.  The cross-axis pixel-index
+// coordinate of the crossing at driving index j is t(j) = alpha + beta j
+// (alpha, beta from FP64 geometry), stored split so that FP32 arithmetic keeps
+// t accurate to ~1e-6 pixel at any image size:
+//   alpha = A + a  (A an integer held exactly in a float, a in [0, 1]),
+//   beta  = bh + bl (bh = beta rounded to FP32, bl the FP32 remainder).
+// The matrix entries are delta * max(0, 1 - |t(j) - k|).
 struct __align__(16) RayF {
-    float alpha, beta, delta;
-    int bits;
+    float A, a, bh, bl;
 };
 
+// Per-ray driving range and axis: bits 0-14 first driving index j_lo,
+// 15-29 last j_hi, 30 driving axis (0: x drives, the image is read through the
+// column-major copy; 1: y drives, row-major copy).  An empty range has
+// j_lo > j_hi.
+__host__ __device__ inline int ray_jlo(int bits) { return bits & 0x7fff; }
+__host__ __device__ inline int ray_jhi(int bits) { return (bits >> 15) & 0x7fff; }
+__host__ __device__ inline int ray_axis(int bits) { return (bits >> 30) & 1; }
+
+// FP64 form (power iteration): t(j) = alpha + beta j in double.
 struct __align__(16) RayD {
     double alpha, beta, delta;
     int bits, pad;
 };
 
-__host__ __device__ inline int ray_jlo(int bits) { return bits & 0x7fff; }
-__host__ __device__ inline int ray_jhi(int bits) { return (bits >> 15) & 0x7fff; }
-__host__ __device__ inline int ray_axis(int bits) { return (bits >> 30) & 1; }
-
 // Per-view back-projection table.  The continuous bin coordinate of the point
 // at pixel-index position (kx, ky) is (n0 + n1 kx + n2 ky) / (d0 + d1 kx + d2 ky) + c
-// (parallel beam: d0 = 1, d1 = d2 = 0).  flags bit 0: the view has x-driven
-// rays, bit 1: y-driven rays.
+// (parallel beam: d0 = 1, d1 = d2 = 0).  Bins [xb0, xb1) hold the view's
+// x-driven rays and [yb0, yb1) its y-driven rays (each contiguous: one of the
+// two ranges is empty unless the fan crosses a diagonal).
 struct __align__(16) ViewRec {
     float n0, n1, n2, c;
-    float d0, d1, d2;
-    int flags;
+    float d0, d1, d2, pad;
+    int xb0, xb1, yb0, yb1;
 };
 
 // Device-side status words of a solve or a norm estimate.
@@ -63,6 +71,8 @@ struct Plan {
     float mu_log2e[kMaxK];         // mu_k * log2(e), FP32
     float C[kMaxK];                // sum_w S[w][k], FP32 (multiplied by I0 per call)
     RayF *rays_f = nullptr;        // [n]
+    int *ray_bits = nullptr;       // [n] driving range and axis
+    float *ray_delta = nullptr;    // [n] step length delta
     RayD *rays_d = nullptr;        // [n]
     ViewRec *views = nullptr;      // [n_views]
     // workspace carve-up (all device pointers inside the bound workspace)
@@ -102,10 +112,12 @@ struct ImgF {
 struct FwdArgs {
     ImgF img;
     const RayF *rays;
+    const int *bits;
+    const float *delta;
     long long n;
     float *z;             // z output (link == false)
     const float *Y;       // collapsed counts (link == true)
-    float *r;             // residual output (link == true)
+    float *r;             // residual output times delta (link == true)
     int K;
     const DevState *state;  // may be null: if set and state->done, return
 };
@@ -122,7 +134,8 @@ struct AdjArgs {
     const RayF *rays;
     const ViewRec *views;
     int n_views, n_bins, nx, ny;
-    const float *r;        // [n] residual (multiplied by each ray's delta on the fly)
+    const float *r;        // [n] residual; already times delta unless `delta` is set
+    const float *delta;    // [n] or null: multiply r by delta on the fly
     float scale;           // out = scale * A^T r   (PLAIN)  |  x_base + scale * A^T r (EG)
     float *out;            // PLAIN: [ny][nx] output
     const float *base_r;   // EG: padded row-major base iterate x_t

@@ -12,10 +12,12 @@
 //     strictly between (kx-1, ky) and (kx+1, ky).
 // Projecting the two end points onto the detector (a ratio of affine forms of
 // (kx, ky), stored per view) bounds the candidate bins; each candidate's weight
-// is then evaluated from the same FP32 ray record and with the same
-// fmaf/floorf expression as the forward walk, so the two kernels use the same
-// matrix entries.  A small margin widens the candidate range; candidates that
+// is then evaluated from the same ray record as the forward walk.  A small margin widens the candidate range; candidates that
 // do not touch the pixel get weight 0.
+//
+// The FP32 weights are formed from the split ray coordinate of k_forward.cu
+// (see weight_f); both kernels reproduce the FP64 matrix entries to ~1e-6, so
+// the gather is the transpose of the forward walk up to FP32 rounding.
 #include "exact_internal.h"
 
 namespace exact {
@@ -45,48 +47,65 @@ __device__ __forceinline__ void bin_range(float num, float den, float dn, float 
     b1 = min(n_bins - 1, (int)floorf(hi));
 }
 
-// Joseph weight of a ray sampling driving index j (given as float jf) for the
-// pixel at cross index k (given as kf): (1 - |t - k|)_+ with t from the record.
-template <typename T, typename R>
-__device__ __forceinline__ T joseph_weight(const R &rec, T jf, T kc)
+// FP32 Joseph weight of ray `rec` at driving index jf for the pixel at cross
+// index kc: max(0, 1 - |u|) with u = t(jf) - kc formed from the split
+// coordinate (t = A + a + (bh + bl) jf): the product bh*jf is split exactly by
+// fmaf, and (A - kc) + bh*jf cancels exactly whenever the ray can touch the
+// pixel, so u carries only FP32 rounding at magnitude ~1.
+__device__ __forceinline__ float weight_f(const RayF &rec, float jf, float kc)
 {
-    const T t = fma(rec.beta, jf, rec.alpha);
-    const T k0 = floor(t);
-    const T f = t - k0;
-    return (k0 == kc) ? T(1) - f : ((k0 == kc - T(1)) ? f : T(0));
+    const float p = rec.bh * jf;
+    const float e = fmaf(rec.bh, jf, -p);
+    const float u = ((rec.A - kc) + p) + (rec.a + fmaf(rec.bl, jf, e));
+    return fmaxf(0.0f, 1.0f - fabsf(u));
 }
 
+// FP64 Joseph weight: t = fma(beta, j, alpha), entries (1 - |t - k|)_+.
+__device__ __forceinline__ double weight_d(const RayD &rec, double jf, double kc)
+{
+    const double u = fma(rec.beta, jf, rec.alpha) - kc;
+    return fmax(0.0, 1.0 - fabs(u)) * rec.delta;
+}
+
+__device__ __forceinline__ float weight_of(const RayF &rec, float jf, float kc) { return weight_f(rec, jf, kc); }
+__device__ __forceinline__ double weight_of(const RayD &rec, double jf, double kc) { return weight_d(rec, jf, kc); }
+
+// A^T r at pixel (kx, ky): the fixed-order sum over views, and within a view
+// over the candidate bins, of weight * r.  For FP32 r must already carry each
+// ray's delta (or `delta` is given); RayD weights include delta.
 template <typename T, typename R, bool FAN>
 __device__ __forceinline__ T gather_pixel(const R *__restrict__ rays, const ViewRec *__restrict__ views,
-                                          const T *__restrict__ r, int n_views, int n_bins, int kx, int ky)
+                                          const T *__restrict__ r, const float *__restrict__ delta, int n_views,
+                                          int n_bins, int kx, int ky)
 {
     const float fx = (float)kx, fy = (float)ky;
     const T tx = (T)kx, ty = (T)ky;
     T acc = T(0);
     for (int v = 0; v < n_views; ++v) {
         const ViewRec vr = views[v];
-        const R *vrays = rays + (long long)v * n_bins;
-        const T *vres = r + (long long)v * n_bins;
+        const long long vb = (long long)v * n_bins;
         const float num = fmaf(vr.n2, fy, fmaf(vr.n1, fx, vr.n0));
         const float den = FAN ? fmaf(vr.d2, fy, fmaf(vr.d1, fx, vr.d0)) : 1.0f;
-        if (vr.flags & 1) {
+        if (vr.xb1 > vr.xb0) {  // x-driven rays sample column kx
             int b0, b1;
             bin_range<FAN>(num, den, vr.n2, vr.d2, vr.c, n_bins, b0, b1);
+            b0 = max(b0, vr.xb0);
+            b1 = min(b1, vr.xb1 - 1);
             for (int b = b0; b <= b1; ++b) {
-                const R rec = vrays[b];
-                if (ray_axis(rec.bits) != 0) continue;
-                const T w = joseph_weight<T>(rec, tx, ty);
-                acc = fma(w * rec.delta, vres[b], acc);
+                const T w = weight_of(rays[vb + b], tx, ty);
+                const T rv = delta ? (T)(r[vb + b] * delta[vb + b]) : r[vb + b];
+                acc = fma(w, rv, acc);
             }
         }
-        if (vr.flags & 2) {
+        if (vr.yb1 > vr.yb0) {  // y-driven rays sample row ky
             int b0, b1;
             bin_range<FAN>(num, den, vr.n1, vr.d1, vr.c, n_bins, b0, b1);
+            b0 = max(b0, vr.yb0);
+            b1 = min(b1, vr.yb1 - 1);
             for (int b = b0; b <= b1; ++b) {
-                const R rec = vrays[b];
-                if (ray_axis(rec.bits) != 1) continue;
-                const T w = joseph_weight<T>(rec, ty, tx);
-                acc = fma(w * rec.delta, vres[b], acc);
+                const T w = weight_of(rays[vb + b], ty, tx);
+                const T rv = delta ? (T)(r[vb + b] * delta[vb + b]) : r[vb + b];
+                acc = fma(w, rv, acc);
             }
         }
     }
@@ -127,7 +146,7 @@ __global__ void __launch_bounds__(TX *TY) k_adjoint(AdjArgs a)
     const int ky = blockIdx.y * TY + threadIdx.y;
     const bool inside = kx < a.nx && ky < a.ny;
     float g = 0.0f;
-    if (inside) g = gather_pixel<float, RayF, FAN>(a.rays, a.views, a.r, a.n_views, a.n_bins, kx, ky);
+    if (inside) g = gather_pixel<float, RayF, FAN>(a.rays, a.views, a.r, a.delta, a.n_views, a.n_bins, kx, ky);
 
     if (MODE == ADJ_PLAIN) {
         if (inside) a.out[(long long)ky * a.nx + kx] = a.scale * g;
@@ -181,7 +200,7 @@ __global__ void __launch_bounds__(TX *TY) k_adjoint_d(const RayD *rays, const Vi
     const bool inside = kx < nx && ky < ny;
     double w = 0.0;
     if (inside) {
-        w = gather_pixel<double, RayD, FAN>(rays, views, zd, n_views, n_bins, kx, ky);
+        w = gather_pixel<double, RayD, FAN>(rays, views, zd, nullptr, n_views, n_bins, kx, ky);
         xrd[(long long)ky * ldr + kx + kPad] = w;
         xcd[(long long)kx * ldc + ky + kPad] = w;
     }

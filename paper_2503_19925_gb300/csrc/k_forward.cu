@@ -10,50 +10,63 @@
 // range [j_lo, j_hi] (computed on the host) leaves out samples that cannot
 // touch the image.  The image (1 MB at 512^2) stays in L1/L2.
 //
-// Link epilogue: r_i = Y_i - sum_k c_k 2^(-mu2_k max(z_i, 0)) with
+// Cross-axis coordinate: t(j) = A + a + (bh + bl) j is re-anchored every
+// kChunk samples.  At the anchor j0 the integer part K and the fraction tau0
+// are formed with an exact product split (fmaf), then inside the chunk
+// tau = fmaf(bh, j - j0, tau0) stays below ~kChunk in magnitude, so FP32 keeps
+// t to ~1e-6 pixel even for 16k-pixel images (a plain fmaf(beta, j, alpha)
+// loses ~3e-5 pixel at 512).
+//
+// Link epilogue: r_i = delta_i (Y_i - sum_k c_k 2^(-mu2_k max(z_i, 0))) with
 // c_k = I0 sum_w S[w][k] and Y_i = sum_w y[w][i] (F is linear in y, so summing
 // the windows first is exact algebra); the per-energy coefficients live in the
-// kernel parameter space (uniform access).
+// kernel parameter space (uniform access).  The residual leaves the kernel
+// already multiplied by the ray's step length, the factor every entry of the
+// ray's row of A carries.
 #include "exact_internal.h"
 
 namespace exact {
 
 namespace {
 
+constexpr int kChunk = 32;
+
 // Sum of the Joseph samples of one ray (without the step length delta).
-// T is the arithmetic type (float on the hot path, double in the power
-// iteration); t = fma(beta, j, alpha) is the same expression the adjoint uses.
-template <typename T, typename R>
-__device__ __forceinline__ T joseph_sum(const T *xr, const T *xc, int nx, int ny, long long ldr, long long ldc,
-                                        const R &rec)
+__device__ __forceinline__ float joseph_sum_f(const ImgF &img, const RayF rec, int bits)
 {
-    const int axis = ray_axis(rec.bits);
-    const int jlo = ray_jlo(rec.bits), jhi = ray_jhi(rec.bits);
-    const T *base = axis ? xr : xc;
-    const long long ld = axis ? ldr : ldc;
-    const int ncross = axis ? nx : ny;
-    const T *row = base + (long long)jlo * ld + kPad;
-    T acc = T(0);
-    T jf = (T)jlo;
+    const int axis = ray_axis(bits);
+    const int jlo = ray_jlo(bits), jhi = ray_jhi(bits);
+    const float *base = axis ? img.xr : img.xc;
+    const long long ld = axis ? img.ldr : img.ldc;
+    const int ncross = axis ? img.nx : img.ny;
+    const int A = (int)rec.A;
+    float acc = 0.0f;
+    for (int j0 = jlo; j0 <= jhi; j0 += kChunk) {
+        // anchor: t(j0) = K + tau0 with tau0 accurate to FP32 rounding at ~1
+        const float jf = (float)j0;
+        const float p = rec.bh * jf;
+        const float e = fmaf(rec.bh, jf, -p);
+        const float P = floorf(p);
+        const float tau0 = ((p - P) + rec.a) + fmaf(rec.bl, jf, e);
+        const int K = A + (int)P;
+        const float *row = base + (long long)j0 * ld + kPad;
+        const int cnt = min(kChunk, jhi - j0 + 1);
+        float di = 0.0f;
 #pragma unroll 4
-    for (int j = jlo; j <= jhi; ++j) {
-        const T t = fma(rec.beta, jf, rec.alpha);
-        const T kf = floor(t);
-        const T f = t - kf;
-        int k = (int)kf;
-        k = min(max(k, -kPad), ncross);
-        const T a0 = __ldg(row + k);
-        const T a1 = __ldg(row + k + 1);
-        acc += fma(f, a1 - a0, a0);
-        row += ld;
-        jf += T(1);
+        for (int i = 0; i < cnt; ++i) {
+            const float tau = fmaf(rec.bh, di, tau0);
+            const float kf = floorf(tau);
+            const float f = tau - kf;
+            int k = K + (int)kf;
+            k = min(max(k, -kPad), ncross);
+            const float a0 = __ldg(row + k);
+            const float a1 = __ldg(row + k + 1);
+            acc += fmaf(f, a1 - a0, a0);
+            row += ld;
+            di += 1.0f;
+        }
     }
     return acc;
-}
-
-__device__ __forceinline__ float joseph_ray(const ImgF &img, const RayF &rec)
-{
-    return rec.delta * joseph_sum<float, RayF>(img.xr, img.xc, img.nx, img.ny, img.ldr, img.ldc, rec);
 }
 
 __global__ void __launch_bounds__(256) k_forward(FwdArgs a)
@@ -61,8 +74,7 @@ __global__ void __launch_bounds__(256) k_forward(FwdArgs a)
     if (a.state && a.state->done) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    const RayF rec = a.rays[i];
-    a.z[i] = joseph_ray(a.img, rec);
+    a.z[i] = a.delta[i] * joseph_sum_f(a.img, a.rays[i], a.bits[i]);
 }
 
 __global__ void __launch_bounds__(256) k_forward_link(FwdArgs a, const LinkCoef coef)
@@ -70,16 +82,16 @@ __global__ void __launch_bounds__(256) k_forward_link(FwdArgs a, const LinkCoef 
     if (a.state && a.state->done) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    const RayF rec = a.rays[i];
-    const float z = joseph_ray(a.img, rec);
+    const float delta = a.delta[i];
+    const float z = delta * joseph_sum_f(a.img, a.rays[i], a.bits[i]);
     const float zp = fmaxf(z, 0.0f);
     float lam = 0.0f;
     for (int k = 0; k < a.K; ++k) lam = fmaf(coef.c[k], exp2f(-coef.mu2[k] * zp), lam);
-    a.r[i] = a.Y[i] - lam;
+    a.r[i] = delta * (a.Y[i] - lam);
 }
 
 // FP64 forward of the power iteration: z = inv_norm * A w, plus per-block
-// partial sums of ||z||^2 (fixed order).
+// partial sums of ||z||^2 (fixed order).  t(j) = fma(beta, j, alpha) in double.
 __global__ void __launch_bounds__(256) k_forward_d(const RayD *rays, long long n, const double *xrd,
                                                    const double *xcd, int nx, int ny, long long ldr,
                                                    long long ldc, double *zd, double *partials,
@@ -90,7 +102,23 @@ __global__ void __launch_bounds__(256) k_forward_d(const RayD *rays, long long n
     double z = 0.0;
     if (i < n) {
         const RayD rec = rays[i];
-        z = st->inv_norm * (rec.delta * joseph_sum<double, RayD>(xrd, xcd, nx, ny, ldr, ldc, rec));
+        const int axis = ray_axis(rec.bits);
+        const int jlo = ray_jlo(rec.bits), jhi = ray_jhi(rec.bits);
+        const double *row = (axis ? xrd : xcd) + (long long)jlo * (axis ? ldr : ldc) + kPad;
+        const long long ld = axis ? ldr : ldc;
+        const int ncross = axis ? nx : ny;
+        double acc = 0.0;
+        for (int j = jlo; j <= jhi; ++j) {
+            const double t = fma(rec.beta, (double)j, rec.alpha);
+            const double kf = floor(t);
+            const double f = t - kf;
+            int k = (int)kf;
+            k = min(max(k, -kPad), ncross);
+            const double a0 = row[k], a1 = row[k + 1];
+            acc += fma(f, a1 - a0, a0);
+            row += ld;
+        }
+        z = st->inv_norm * (rec.delta * acc);
         zd[i] = z;
     }
     double s = z * z;

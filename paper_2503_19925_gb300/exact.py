@@ -187,6 +187,7 @@ class Plan:
                 torch.cuda.synchronize(self.device)
                 load().exact_plan_destroy(self._h)
             self._h = None
+            self._pending = []
 
     def __del__(self):
         try:
@@ -246,11 +247,16 @@ class Plan:
         self._t(x, self.shape_img, name="x")
         opts = _SolveOpts(float(lo), float(hi), float(tol), int(check_every), int(bool(average_tail)))
         info = _SolveInfo()
-        self._info = info  # keep alive until the host callback has run
         _check("exact_solve", load().exact_solve(self._h, _ptr(y), dt, float(I0), float(eta), int(iters),
                                                  ctypes.byref(opts), _ptr(x), ctypes.byref(info), _stream()))
+        # the library writes `info` from a stream callback: keep it alive until
+        # the stream has passed the end of this solve
+        done = torch.cuda.Event()
+        done.record()
+        self._pending = [(e, i) for e, i in getattr(self, "_pending", []) if not e.query()]
+        self._pending.append((done, info))
         if sync:
-            torch.cuda.current_stream().synchronize()
+            done.synchronize()
         return x, info
 
     def norm_estimate(self, max_iters: int = 500, rtol: float = 1e-9):
