@@ -197,7 +197,8 @@ size_t carve(Plan &P, char *base)
     P.r = c.take<float>(base, (size_t)P.n);
     const int nb_adj = adjoint_blocks(P.g.nx, P.g.ny);
     const int nb_fwd = forward_d_blocks(P.n);
-    P.partials = c.take<double>(base, (size_t)(2 * nb_adj + nb_fwd + nb_adj));
+    const int nb_adj_d = adjoint_d_blocks(P.g.nx, P.g.ny);
+    P.partials = c.take<double>(base, (size_t)(2 * nb_adj + nb_fwd + nb_adj_d));
     P.avg = c.take<double>(base, (size_t)P.d);
     P.xrd = c.take<double>(base, (size_t)(ny * P.ldr()));
     P.xcd = c.take<double>(base, (size_t)(nx * P.ldc()));
@@ -671,6 +672,7 @@ exact_status exact_norm_estimate(exact_plan_t plan, int max_iters, double rtol, 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int nb_adj = adjoint_blocks(P.g.nx, P.g.ny);
     const int nb_fwd = forward_d_blocks(P.n);
+    const int nb_adj_d = adjoint_d_blocks(P.g.nx, P.g.ny);
     double *pz = P.partials + 2 * nb_adj;
     double *pw = pz + nb_fwd;
     const bool fan = P.g.beam == 1;
@@ -683,7 +685,7 @@ exact_status exact_norm_estimate(exact_plan_t plan, int max_iters, double rtol, 
                                        P.state, s));
             EXACT_TRY(launch_adjoint_d(P.rays_d, P.views, P.g.n_views, P.g.n_bins, P.g.nx, P.g.ny, P.zd, P.xrd,
                                        P.xcd, P.ldr(), P.ldc(), pw, P.state, fan, s));
-            EXACT_TRY(launch_power_reduce(pz, nb_fwd, pw, nb_adj, P.state, it, rtol, s));
+            EXACT_TRY(launch_power_reduce(pz, nb_fwd, pw, nb_adj_d, P.state, it, rtol, s));
         }
         EXACT_TRY(cudaMemcpyAsync(P.host_state, P.state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
         EXACT_TRY(cudaStreamSynchronize(s));

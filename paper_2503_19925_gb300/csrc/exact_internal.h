@@ -153,7 +153,8 @@ struct AdjArgs {
 // ---- launchers (each returns cudaGetLastError()) ------------------------------
 cudaError_t launch_forward(const FwdArgs &a, bool link, const LinkCoef *coef, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjArgs &a, int mode, bool fan, cudaStream_t s);
-int adjoint_blocks(int nx, int ny);
+int adjoint_blocks(int nx, int ny);    // blocks (= partial-norm pairs) of the FP32 adjoint
+int adjoint_d_blocks(int nx, int ny);  // blocks (= partial sums) of the FP64 adjoint
 
 cudaError_t launch_pack(const float *x, float *xr, float *xc, int nx, int ny, long long ldr, long long ldc,
                         float lo, float hi, bool project, cudaStream_t s);
