@@ -129,6 +129,32 @@ RayHost make_ray(const exact_geometry &g, int v, int b)
     return r;
 }
 
+// Replays, with the same FP32 operations as joseph_sum_f in k_forward.cu, the
+// cross index of the first and last sample of every 32-sample chunk of a ray
+// and checks that the two interpolation taps stay inside the padded image row
+// ([-kPad, n_cross + kPad - 1]).  Within a chunk the index is monotone in the
+// sample number, so the chunk ends bound it.  (This file is compiled with FP
+// contraction off, so the host arithmetic matches the device expression.)
+bool taps_in_bounds(const RayF &r, int bits, int ncross)
+{
+    const int jlo = ray_jlo(bits), jhi = ray_jhi(bits);
+    for (int j0 = jlo; j0 <= jhi; j0 += 32) {
+        const float jf = (float)j0;
+        const float p = r.bh * jf;
+        const float e = fmaf(r.bh, jf, -p);
+        const float P = floorf(p);
+        const float tau0 = ((p - P) + r.a) + fmaf(r.bl, jf, e);
+        const int cnt = (jhi - j0 + 1) < 32 ? (jhi - j0 + 1) : 32;
+        const float ends[2] = {tau0, fmaf(r.bh, (float)(cnt - 1), tau0)};
+        for (float tau : ends) {
+            if (!(fabsf(tau) < 4194304.0f)) return false;
+            const long long k0 = (long long)r.A + (long long)P + (long long)floorf(tau);
+            if (k0 < -kPad || k0 + 1 > (long long)ncross + kPad - 1) return false;
+        }
+    }
+    return true;
+}
+
 ViewRec make_view(const exact_geometry &g, int v, int xb0, int xb1, int yb0, int yb1)
 {
     const double th = g.angle0 + (double)v * g.angle_range / (double)g.n_views;
@@ -379,6 +405,10 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
             rf[i].bl = (float)(h.beta - (double)bh);
             rbits[i] = bits;
             rdelta[i] = (float)h.delta;
+            if (!taps_in_bounds(rf[i], bits, h.axis ? g.nx : g.ny)) {
+                delete P;
+                return EXACT_ERR_UNSUPPORTED;
+            }
             rd[i].alpha = h.alpha;
             rd[i].beta = h.beta;
             rd[i].delta = h.delta;

@@ -12,6 +12,12 @@ namespace exact {
 // Zero columns kept on each side of a padded image row so that a Joseph sample
 // at cross index k0 in [-2, n_cross] can read k0 and k0+1 without a bounds test.
 constexpr int kPad = 2;
+
+// floor(v) of a float with |v| < 2^22 without the conversion pipe:
+// r = v + 1.5 * 2^23 rounded down holds floor(v) in its low mantissa bits,
+// floor(v) = r - kFloorMagic exactly and = bits(r) - kFloorBias as an integer.
+constexpr float kFloorMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr int kFloorBias = 0x4B400000;      // bit pattern of kFloorMagic
 constexpr int kMaxK = EXACT_MAX_ENERGY;
 
 // One ray of the Joseph projector, FP32 form.  The cross-axis pixel-index

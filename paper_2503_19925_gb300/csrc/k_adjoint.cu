@@ -4,16 +4,16 @@
 // stopping rule.
 //
 // FP32 kernel (hot path): one CTA owns a tile of kTW x kTH pixels; its kG warps
-// split the views into kG contiguous chunks.  For each view a warp walks the
-// rays that cross the tile:
+// split the views (warp g takes views g, g + kG, ...; interleaving keeps the
+// warps' loads even).  For each view a warp walks the rays that cross the tile:
 //   - x-driven rays sample every pixel column; lane l owns column tx0 + l and
 //     walks, in bin order, the rays whose crossing with that column lies
 //     strictly inside (ty0 - 1, ty0 + kTH).  Each ray adds (1 - f) r and f r
 //     to the two pixels around its crossing (the two nonzero entries of its
 //     row of A in this column);
-//   - y-driven rays sample every pixel row; lane l owns half a row (row
-//     ty0 + l % kTH, kTH columns starting at tx0 + kTH (l / kTH)) and walks
-//     its rays the same way.
+//   - y-driven rays sample every pixel row; lane l owns a segment of a row
+//     (row ty0 + l % kTH, kTH columns starting at tx0 + kTH (l / kTH)) and
+//     walks its rays the same way.
 // The rays crossing a strip form one contiguous bin range: the two end points
 // of the strip projected onto the detector (a ratio of affine forms of the
 // pixel coordinates, stored per view) bound it.  Each lane accumulates into
@@ -39,10 +39,11 @@ constexpr float kBinEps = 0.01f;
 // ---------------------------------------------------------------- FP32 strip walk
 
 constexpr int kTW = 32;        // tile width (pixels) = lanes of a warp
-constexpr int kTH = 16;        // tile height = strip length of the x-driven walk
-constexpr int kG = 8;          // warps per CTA (view chunks)
+constexpr int kTH = 8;         // tile height = strip length of both walks
+constexpr int kG = 6;          // warps per CTA (view subsets)
 constexpr int kRows = kTH + 2; // accumulator rows: strip offsets -1 .. kTH
-static_assert(kTW == 2 * kTH, "y-driven lanes cover two half rows of kTH pixels");
+constexpr int kSeg = kTW / kTH; // y-driven lanes: kSeg segments of kTH columns per row
+static_assert(kTW % kTH == 0, "y-driven lanes split a tile row into whole segments");
 
 // Bin range of the rays that cross the segment between two points whose
 // detector projections are (num1/den1, num2/den2) + c, within [lo_bin, hi_bin).
@@ -75,9 +76,10 @@ __device__ __forceinline__ void strip_walk(const RayF *__restrict__ vrays, const
         const float p = rec.bh * jf;
         const float e = fmaf(rec.bh, jf, -p);
         const float u = ((rec.A - kbase) + p) + (rec.a + fmaf(rec.bl, jf, e));
-        const float kf = floorf(u);
-        const float f = u - kf;
-        const int k = (int)kf;
+        // floor(u) without the conversion pipe (|u| < 2^22)
+        const float r = __fadd_rd(u, kFloorMagic);
+        const float f = u - (r - kFloorMagic);
+        const int k = __float_as_int(r) - kFloorBias;
         if (k >= -1 && k < kTH) {
             const float w1 = f * rv;
             acc[(k + 1) * kTW + lane] += rv - w1;
@@ -87,7 +89,7 @@ __device__ __forceinline__ void strip_walk(const RayF *__restrict__ vrays, const
 }
 
 template <int MODE, bool FAN, bool DELTA>
-__global__ void __launch_bounds__(kG * 32) k_adjoint(AdjArgs a)
+__global__ void __launch_bounds__(kG * 32, 8) k_adjoint(AdjArgs a)
 {
     if (a.state && a.state->done) return;
     extern __shared__ float smem[];
@@ -114,9 +116,7 @@ __global__ void __launch_bounds__(kG * 32) k_adjoint(AdjArgs a)
     const bool yok = ry < a.ny && cy0 < a.nx;
     const float fry = (float)ry, fx_lo = (float)(cy0 - 1), fx_hi = (float)min(cy0 + kTH, a.nx);
 
-    const int v_begin = (int)(((long long)a.n_views * g) / kG);
-    const int v_end = (int)(((long long)a.n_views * (g + 1)) / kG);
-    for (int v = v_begin; v < v_end; ++v) {
+    for (int v = g; v < a.n_views; v += kG) {
         const ViewRec vr = a.views[v];
         const long long vb = (long long)v * a.n_bins;
         const RayF *vrays = a.rays + vb;

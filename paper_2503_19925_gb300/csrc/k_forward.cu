@@ -32,13 +32,17 @@ namespace {
 constexpr int kChunk = 32;
 
 // Sum of the Joseph samples of one ray (without the step length delta).
+// Bounds: the host range [j_lo, j_hi] keeps the exact crossing t(j) inside
+// (-1.5, n_cross + 0.5) and the FP32 evaluation below is within 1e-5 of it,
+// so k0 = floor(t) lies in [-2, n_cross] and the taps k0, k0 + 1 stay inside the
+// padded row [-kPad, n_cross + kPad - 1]; exact_plan_create re-checks this for
+// every chunk anchor and chunk end with the same FP32 operations.
 __device__ __forceinline__ float joseph_sum_f(const ImgF &img, const RayF rec, int bits)
 {
     const int axis = ray_axis(bits);
     const int jlo = ray_jlo(bits), jhi = ray_jhi(bits);
-    const float *base = axis ? img.xr : img.xc;
-    const long long ld = axis ? img.ldr : img.ldc;
-    const int ncross = axis ? img.nx : img.ny;
+    const float *__restrict__ base = (axis ? img.xr : img.xc) + kPad;
+    const int ld = (int)(axis ? img.ldr : img.ldc);
     const int A = (int)rec.A;
     float acc = 0.0f;
     for (int j0 = jlo; j0 <= jhi; j0 += kChunk) {
@@ -48,28 +52,30 @@ __device__ __forceinline__ float joseph_sum_f(const ImgF &img, const RayF rec, i
         const float e = fmaf(rec.bh, jf, -p);
         const float P = floorf(p);
         const float tau0 = ((p - P) + rec.a) + fmaf(rec.bl, jf, e);
-        const int K = A + (int)P;
-        const float *row = base + (long long)j0 * ld + kPad;
+        // element offset of the row start plus K, minus the bias of the
+        // float-to-int trick below
+        int off = j0 * ld + A + (int)P - kFloorBias;
         const int cnt = min(kChunk, jhi - j0 + 1);
         float di = 0.0f;
 #pragma unroll 4
         for (int i = 0; i < cnt; ++i) {
             const float tau = fmaf(rec.bh, di, tau0);
-            const float kf = floorf(tau);
-            const float f = tau - kf;
-            int k = K + (int)kf;
-            k = min(max(k, -kPad), ncross);
-            const float a0 = __ldg(row + k);
-            const float a1 = __ldg(row + k + 1);
+            // floor(tau) for |tau| < 2^22: round-down add of 1.5 * 2^23 leaves
+            // floor(tau) in the low mantissa bits
+            const float r = __fadd_rd(tau, kFloorMagic);
+            const float f = tau - (r - kFloorMagic);
+            const int idx = off + __float_as_int(r);
+            const float a0 = __ldg(base + idx);
+            const float a1 = __ldg(base + idx + 1);
             acc += fmaf(f, a1 - a0, a0);
-            row += ld;
+            off += ld;
             di += 1.0f;
         }
     }
     return acc;
 }
 
-__global__ void __launch_bounds__(256) k_forward(FwdArgs a)
+__global__ void __launch_bounds__(256, 8) k_forward(FwdArgs a)
 {
     if (a.state && a.state->done) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,7 +83,7 @@ __global__ void __launch_bounds__(256) k_forward(FwdArgs a)
     a.z[i] = a.delta[i] * joseph_sum_f(a.img, a.rays[i], a.bits[i]);
 }
 
-__global__ void __launch_bounds__(256) k_forward_link(FwdArgs a, const LinkCoef coef)
+__global__ void __launch_bounds__(256, 8) k_forward_link(FwdArgs a, const LinkCoef coef)
 {
     if (a.state && a.state->done) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
