@@ -3,6 +3,8 @@
 // that enqueue the kernels of k_forward.cu, k_adjoint.cu and k_util.cu.
 #include "exact_internal.h"
 
+#include <climits>
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <new>
 #include <string.h>
@@ -129,30 +131,129 @@ RayHost make_ray(const exact_geometry &g, int v, int b)
     return r;
 }
 
-// Replays, with the same FP32 operations as joseph_sum_f in k_forward.cu, the
-// cross index of the first and last sample of every 32-sample chunk of a ray
-// and checks that the two interpolation taps stay inside the padded image row
-// ([-kPad, n_cross + kPad - 1]).  Within a chunk the index is monotone in the
-// sample number, so the chunk ends bound it.  (This file is compiled with FP
-// contraction off, so the host arithmetic matches the device expression.)
-bool taps_in_bounds(const RayF &r, int bits, int ncross)
+// Cross index k0 = floor(t(j)) of a ray at driving index j, replayed with the
+// same FP32 operations as k_forward_tma (anchor at the chunk start j0, then
+// fmaf(bh, j - j0, tau0)).  This file is compiled with FP contraction off, so
+// the host arithmetic matches the device expression.
+long long k0_at(const RayF &r, int j)
 {
-    const int jlo = ray_jlo(bits), jhi = ray_jhi(bits);
-    for (int j0 = jlo; j0 <= jhi; j0 += 32) {
-        const float jf = (float)j0;
-        const float p = r.bh * jf;
-        const float e = fmaf(r.bh, jf, -p);
-        const float P = floorf(p);
-        const float tau0 = ((p - P) + r.a) + fmaf(r.bl, jf, e);
-        const int cnt = (jhi - j0 + 1) < 32 ? (jhi - j0 + 1) : 32;
-        const float ends[2] = {tau0, fmaf(r.bh, (float)(cnt - 1), tau0)};
-        for (float tau : ends) {
-            if (!(fabsf(tau) < 4194304.0f)) return false;
-            const long long k0 = (long long)r.A + (long long)P + (long long)floorf(tau);
-            if (k0 < -kPad || k0 + 1 > (long long)ncross + kPad - 1) return false;
+    const int j0 = (j / kFC) * kFC;
+    const float jf = (float)j0;
+    const float p = r.bh * jf;
+    const float e = fmaf(r.bh, jf, -p);
+    const float P = floorf(p);
+    const float tau0 = ((p - P) + r.a) + fmaf(r.bl, jf, e);
+    const float tau = fmaf(r.bh, (float)(j - j0), tau0);
+    return (long long)r.A + (long long)P + (long long)floorf(tau);
+}
+
+// Work unit over rays [b, b + cnt) of one view segment: the chunks their
+// driving ranges cover and, per chunk, the first staged cross row.  Within a
+// view the crossing t_b(j) is monotone in b at every j (rays of a fan or a
+// parallel view do not cross inside the image), so the first and last ray
+// that sample a chunk bound all others; a row of margin on each side absorbs
+// FP32 rounding.  Returns false if a band does not fit in kFHB rows.
+bool make_unit(const RayF *rf, const int *bits, long long ray0, int cnt, int axis, FwdUnit &u,
+               std::vector<int> &kst)
+{
+    int jmin = 1 << 30, jmax = -1;
+    for (int q = 0; q < cnt; ++q) {
+        const int lo = ray_jlo(bits[ray0 + q]), hi = ray_jhi(bits[ray0 + q]);
+        if (lo <= hi) {
+            jmin = lo < jmin ? lo : jmin;
+            jmax = hi > jmax ? hi : jmax;
+        }
+    }
+    u.ray0 = (int)ray0;
+    u.count = cnt;
+    u.axis = axis;
+    u.pad0 = u.pad1 = 0;
+    u.koff = (int)kst.size();
+    if (jmax < 0) {
+        u.jc0 = 0;
+        u.nchunks = 0;
+        return true;
+    }
+    u.jc0 = jmin / kFC;
+    u.nchunks = jmax / kFC - u.jc0 + 1;
+    std::vector<int> local;
+    for (int c = 0; c < u.nchunks; ++c) {
+        const int j0 = (u.jc0 + c) * kFC, j1 = j0 + kFC - 1;
+        int qf = -1, ql = -1;
+        for (int q = 0; q < cnt; ++q) {
+            const int lo = ray_jlo(bits[ray0 + q]), hi = ray_jhi(bits[ray0 + q]);
+            if (lo <= j1 && hi >= j0 && lo <= hi) {
+                if (qf < 0) qf = q;
+                ql = q;
+            }
+        }
+        if (qf < 0) {  // no ray samples this chunk: stage nothing useful, any aligned start
+            local.push_back(-kPad);
+            continue;
+        }
+        long long kmin = LLONG_MAX, kmax = LLONG_MIN;
+        for (int q : {qf, ql})
+            for (int j : {j0, j1}) {
+                const long long k = k0_at(rf[ray0 + q], j);
+                kmin = k < kmin ? k : kmin;
+                kmax = k > kmax ? k : kmax;
+            }
+        // rows kmin - 1 .. kmax + 2 (taps k0, k0 + 1 and a row of margin each side)
+        long long start = kmin - 1 + kPad;
+        start = (start >= 0 ? start / 4 : -((-start + 3) / 4)) * 4 - kPad;
+        if (kmax + 2 - start > kFHB - 1) return false;
+        if (start < INT_MIN / 2 || start > INT_MAX / 2) return false;
+        local.push_back((int)start);
+    }
+    kst.insert(kst.end(), local.begin(), local.end());
+    return true;
+}
+
+// Splits every view segment into work units of at most kFR rays whose bands fit.
+bool build_units(const exact_geometry &g, const std::vector<RayF> &rf, const std::vector<int> &rbits,
+                 const std::vector<ViewRec> &vw, std::vector<FwdUnit> &units, std::vector<int> &kst)
+{
+    for (int v = 0; v < g.n_views; ++v) {
+        const long long vb = (long long)v * g.n_bins;
+        const int segs[2][3] = {{vw[v].xb0, vw[v].xb1, 0}, {vw[v].yb0, vw[v].yb1, 1}};
+        for (const auto &sg : segs) {
+            int b = sg[0];
+            while (b < sg[1]) {
+                int cnt = sg[1] - b < kFR ? sg[1] - b : kFR;
+                FwdUnit u;
+                while (!make_unit(rf.data(), rbits.data(), vb + b, cnt, sg[2], u, kst)) {
+                    if (cnt == 1) return false;
+                    cnt = cnt * 3 / 4 > 1 ? cnt * 3 / 4 : 1;
+                }
+                units.push_back(u);
+                b += cnt;
+            }
         }
     }
     return true;
+}
+
+// Encodes the 2D tensor map (x = padded cross index, y = driving line) of one
+// padded image copy; box kFHB x kFC, zero fill outside.
+bool encode_map(CUtensorMap *map, float *base, long long ld, long long lines)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *ptr = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !ptr)
+            return false;
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)lines};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kFHB, (cuuint32_t)kFC};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 ViewRec make_view(const exact_geometry &g, int v, int xb0, int xb1, int yb0, int yb1)
@@ -405,10 +506,6 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
             rf[i].bl = (float)(h.beta - (double)bh);
             rbits[i] = bits;
             rdelta[i] = (float)h.delta;
-            if (!taps_in_bounds(rf[i], bits, h.axis ? g.nx : g.ny)) {
-                delete P;
-                return EXACT_ERR_UNSUPPORTED;
-            }
             rd[i].alpha = h.alpha;
             rd[i].beta = h.beta;
             rd[i].delta = h.delta;
@@ -434,7 +531,19 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
         }
         vw[v] = make_view(g, v, xb0, xb1, yb0, yb1);
     }
+    std::vector<FwdUnit> units;
+    std::vector<int> kst;
+    if (!build_units(g, rf, rbits, vw, units, kst)) {
+        delete P;
+        return EXACT_ERR_UNSUPPORTED;
+    }
+    if (kst.empty()) kst.push_back(0);
+    P->n_units = (int)units.size();
     cudaError_t e = cudaMalloc(&P->rays_f, sizeof(RayF) * rf.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->units, sizeof(FwdUnit) * units.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->kstart, sizeof(int) * kst.size());
+    if (e == cudaSuccess) e = cudaMemcpy(P->units, units.data(), sizeof(FwdUnit) * units.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->kstart, kst.data(), sizeof(int) * kst.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&P->ray_bits, sizeof(int) * rbits.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->ray_delta, sizeof(float) * rdelta.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->rays_d, sizeof(RayD) * rd.size());
@@ -463,6 +572,8 @@ exact_status exact_plan_destroy(exact_plan_t plan)
     cudaGetDevice(&prev);
     if (P->device >= 0 && prev != P->device) cudaSetDevice(P->device);
     if (P->rays_f) cudaFree(P->rays_f);
+    if (P->units) cudaFree(P->units);
+    if (P->kstart) cudaFree(P->kstart);
     if (P->ray_bits) cudaFree(P->ray_bits);
     if (P->ray_delta) cudaFree(P->ray_delta);
     if (P->rays_d) cudaFree(P->rays_d);
@@ -507,9 +618,17 @@ exact_status exact_plan_bind_workspace(exact_plan_t plan, void *dev_ptr, size_t 
         cudaGetLastError();
         return EXACT_ERR_INVALID_ARG;
     }
+    carve(*P, static_cast<char *>(dev_ptr));
+    for (int q = 0; q < 2; ++q) {
+        if (!encode_map(&P->maps_r[q], P->xr[q], P->ldr(), P->g.ny) ||
+            !encode_map(&P->maps_c[q], P->xc[q], P->ldc(), P->g.nx)) {
+            P->ws = nullptr;
+            P->ws_bytes = 0;
+            return EXACT_ERR_CUDA;
+        }
+    }
     P->ws = dev_ptr;
     P->ws_bytes = bytes;
-    carve(*P, static_cast<char *>(dev_ptr));
     return EXACT_OK;
 }
 
@@ -527,9 +646,12 @@ exact_status exact_forward(exact_plan_t plan, const float *x, float *z, exact_st
     a.rays = P.rays_f;
     a.bits = P.ray_bits;
     a.delta = P.ray_delta;
+    a.units = P.units;
+    a.kstart = P.kstart;
+    a.n_units = P.n_units;
     a.n = P.n;
     a.z = z;
-    EXACT_TRY(launch_forward(a, false, nullptr, s));
+    EXACT_TRY(launch_forward(a, false, nullptr, P.maps_r[0], P.maps_c[0], s));
     return EXACT_OK;
 }
 
@@ -574,11 +696,14 @@ exact_status exact_operator(exact_plan_t plan, const float *x, const void *y, ex
     f.rays = P.rays_f;
     f.bits = P.ray_bits;
     f.delta = P.ray_delta;
+    f.units = P.units;
+    f.kstart = P.kstart;
+    f.n_units = P.n_units;
     f.n = P.n;
     f.Y = P.Y;
     f.r = P.r;
     f.K = P.K;
-    EXACT_TRY(launch_forward(f, true, &coef, s));
+    EXACT_TRY(launch_forward(f, true, &coef, P.maps_r[0], P.maps_c[0], s));
     AdjArgs a;
     memset(&a, 0, sizeof(a));
     a.rays = P.rays_f;
@@ -625,6 +750,10 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     f.rays = P.rays_f;
     f.bits = P.ray_bits;
     f.delta = P.ray_delta;
+    f.units = P.units;
+    f.kstart = P.kstart;
+    f.n_units = P.n_units;
+    f.err = P.state;
     f.n = P.n;
     f.Y = P.Y;
     f.r = P.r;
@@ -655,7 +784,7 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
         // half step: x_{t+1/2} = P(x_t - eta F(x_t))
         f.img = img_of(P, 0);
         u = prof_begin(P, 0, t, s);
-        EXACT_TRY(launch_forward(f, true, &coef, s));
+        EXACT_TRY(launch_forward(f, true, &coef, P.maps_r[0], P.maps_c[0], s));
         prof_end(P, u, s);
         a.out_r = P.xr[1];
         a.out_c = P.xc[1];
@@ -666,7 +795,7 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
         // full step from the same base: x_{t+1} = P(x_t - eta F(x_{t+1/2}))
         f.img = img_of(P, 1);
         u = prof_begin(P, 0, t, s);
-        EXACT_TRY(launch_forward(f, true, &coef, s));
+        EXACT_TRY(launch_forward(f, true, &coef, P.maps_r[1], P.maps_c[1], s));
         prof_end(P, u, s);
         a.out_r = P.xr[0];
         a.out_c = P.xc[0];

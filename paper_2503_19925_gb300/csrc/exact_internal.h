@@ -1,6 +1,7 @@
 // exact_internal.h -- types shared by the host plan code and the kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -56,6 +57,19 @@ struct __align__(16) ViewRec {
     int xb0, xb1, yb0, yb1;
 };
 
+// Forward-projector work unit: up to kFR adjacent rays of one view with one
+// driving axis.  The image band these rays cross in driving lines
+// [c kFC, (c + 1) kFC) is staged in shared memory as a kFC x kFHB box whose
+// first row is cross index kstart[koff + c - jc0] (a multiple of 4 after
+// adding kPad, as the tensor-map x coordinate must be 16-byte aligned).
+constexpr int kFR = 128;   // rays per unit (threads per CTA)
+constexpr int kFC = 16;    // driving lines per staged chunk
+constexpr int kFHB = 256;  // staged cross-axis rows per chunk (tensor-map box height)
+struct __align__(16) FwdUnit {
+    int ray0, count, axis, jc0;
+    int nchunks, koff, pad0, pad1;
+};
+
 // Device-side status words of a solve or a norm estimate.
 struct DevState {
     int done;         // nonzero: later kernels of this solve return at once
@@ -96,14 +110,22 @@ struct Plan {
     // pinned host mirror of the device state (solve info)
     DevState *host_state = nullptr;
     long long nnz = 0;              // nonzero entries of A
+    FwdUnit *units = nullptr;       // [n_units] forward work units
+    int *kstart = nullptr;          // [n_kstart] staged band start per unit chunk
+    int n_units = 0;
+    // tensor maps of the padded copies: maps_r[q] over xr[q], maps_c[q] over xc[q]
+    CUtensorMap maps_r[2], maps_c[2];
+    bool maps_ok = false;
     // kernel timing (profiling aid): event pairs recorded around sampled launches
     int prof_every = 0;
     int prof_used = 0;              // event pairs recorded since the last read
     int prof_cap = 0;
     cudaEvent_t *prof_ev = nullptr; // [2 * prof_cap]
     int *prof_kind = nullptr;       // [prof_cap]
-    long long ldr() const { return g.nx + 2 * kPad; }
-    long long ldc() const { return g.ny + 2 * kPad; }
+    // padded row lengths, rounded up to 4 floats so rows start on 16-byte
+    // boundaries (tensor-map strides must be multiples of 16 bytes)
+    long long ldr() const { return (g.nx + 2 * kPad + 3) / 4 * 4; }
+    long long ldc() const { return (g.ny + 2 * kPad + 3) / 4 * 4; }
 };
 
 // ---- launch parameter blocks -------------------------------------------------
@@ -120,6 +142,10 @@ struct FwdArgs {
     const RayF *rays;
     const int *bits;
     const float *delta;
+    const FwdUnit *units;
+    const int *kstart;
+    int n_units;
+    DevState *err;          // where a timed-out staging wait is reported (may be null)
     long long n;
     float *z;             // z output (link == false)
     const float *Y;       // collapsed counts (link == true)
@@ -157,7 +183,8 @@ struct AdjArgs {
 };
 
 // ---- launchers (each returns cudaGetLastError()) ------------------------------
-cudaError_t launch_forward(const FwdArgs &a, bool link, const LinkCoef *coef, cudaStream_t s);
+cudaError_t launch_forward(const FwdArgs &a, bool link, const LinkCoef *coef, const CUtensorMap &map_r,
+                           const CUtensorMap &map_c, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjArgs &a, int mode, bool fan, cudaStream_t s);
 int adjoint_blocks(int nx, int ny);    // blocks (= partial-norm pairs) of the FP32 adjoint
 int adjoint_d_blocks(int nx, int ny);  // blocks (= partial sums) of the FP64 adjoint

@@ -44,14 +44,12 @@ __global__ void k_pack_cols(const float *x, float *xc, int nx, int ny, long long
         const int ix = bx + r, iy = by + threadIdx.x;
         if (ix < nx && iy < ny) xc[(long long)ix * ldc + iy + kPad] = tile[threadIdx.x][r];
     }
-    // pads of the rows this block owns
+    // pads (and the alignment tail) of the rows this block owns
     if (blockIdx.y == 0 && threadIdx.y == 0 && threadIdx.x < 32) {
         const int ix = bx + threadIdx.x;
         if (ix < nx) {
-            for (int p = 0; p < kPad; ++p) {
-                xc[(long long)ix * ldc + p] = 0.0f;
-                xc[(long long)ix * ldc + kPad + ny + p] = 0.0f;
-            }
+            for (int p = 0; p < kPad; ++p) xc[(long long)ix * ldc + p] = 0.0f;
+            for (long long p = kPad + ny; p < ldc; ++p) xc[(long long)ix * ldc + p] = 0.0f;
         }
     }
 }
