@@ -52,6 +52,13 @@ def parse_args(argv=None):
     p.add_argument("--cpu-baseline-iters", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-every", type=int, default=10)
+    p.add_argument("--no-batched", action="store_true", help="skip the batched-vs-sequential measurement")
+    p.add_argument("--batch-jobs", type=int, default=64)
+    p.add_argument("--batch-iters", type=int, default=None)
+    p.add_argument("--no-served", action="store_true", help="skip the serving measurement")
+    p.add_argument("--serve-jobs", type=int, default=32)
+    p.add_argument("--serve-load", type=float, default=0.8,
+                   help="arrival rate as a fraction of the measured sequential capacity")
     return p.parse_args(argv)
 
 
@@ -233,6 +240,171 @@ def load_traffic(kernel: str):
     return None
 
 
+def make_counts(ex, torch, spec, dev, rank=0):
+    """Plan, counts and ground truth of one synthetic job (counts from this
+    path's own projector, Poisson, seeded)."""
+    g = spec["geometry"]
+    n = max(g["nx"], g["ny"])
+    e = synth.energy_grid(spec["K"])
+    S = synth.window_partition(spec["K"], spec["W"]) * synth.smooth_spectrum(e, spec["seed"])[None, :]
+    mu = synth.power_law_mu(e, configs.mu_scale(n))
+    xs = synth.rasterize_ellipses(synth.random_ellipses(n, 6, spec["seed"]), g["nx"], g["ny"], supersample=2)
+    plan = ex.Plan(ex.Geometry(**g), mu, S)
+    z = plan.forward(torch.tensor(xs, dtype=torch.float32, device=dev)).double()
+    lam = spec["I0"] * torch.einsum("wk,kvb->wvb", torch.tensor(S, dtype=torch.float64, device=dev),
+                                    torch.exp(-torch.tensor(mu, dtype=torch.float64, device=dev)[:, None, None]
+                                              * z.clamp_min(0)[None]))
+    gen = torch.Generator(device=dev).manual_seed(spec["seed"] + 7919 * rank)
+    y = torch.poisson(lam, generator=gen).to(torch.float32).contiguous()
+    return plan, y, mu, S, xs
+
+
+def run_served(ex, torch, dev, n_jobs: int, load: float, rank: int):
+    """A Poisson stream of reconstruction requests (image sizes 128..512,
+    90..720 views, parallel or fan beam, 1..4 windows, 16..64 energies,
+    tolerance 1e-3) served (a) by the continuous-batching Server and (b) one at
+    a time with exact_solve, at an arrival rate of `load` times the measured
+    one-at-a-time capacity.  Plan building, upload and the step-size estimate
+    of each request are inside the served time in both cases."""
+    from paper_2503_19925_gb300.serve import Request, Server, serve_sequential
+    specs = configs.c5_requests(n_jobs, sizes=(128, 512), views=(90, 720))
+    reqs, truth = [], {}
+    for k, sp in enumerate(specs):
+        plan, y, mu, S, xs = make_counts(ex, torch, sp, dev, rank)
+        plan.close()
+        reqs.append(Request(ex.Geometry(**sp["geometry"]), list(mu), S.tolist(), y.cpu().pin_memory(), sp["I0"],
+                            tol=1e-3, max_iters=1000, tag=k))
+        truth[k] = xs
+    torch.cuda.synchronize()
+
+    def summarise(results):
+        t_first = min(r.arrival for r in results)
+        t_last = max(r.finished for r in results)
+        lat = sorted(r.latency for r in results)
+        ps = [20 * math.log10(1.0 / float(np.sqrt(np.mean((r.x.double().numpy() - truth[r.tag]) ** 2))))
+              for r in results]
+        return {"recon_per_s": len(results) / (t_last - t_first), "p50_latency_s": lat[len(lat) // 2],
+                "p99_latency_s": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                "mean_psnr_db": float(np.mean(ps)), "mean_iters": float(np.mean([r.iters for r in results]))}
+
+    for r in reqs:
+        r.arrival = 0.0
+    cap = summarise(serve_sequential(reqs, realtime=False))["recon_per_s"]
+    rate = load * cap
+    rng = np.random.default_rng(55)
+    t = 0.0
+    for r in reqs:
+        t += float(rng.exponential(1.0 / rate))
+        r.arrival = t
+    server = Server(budget_bytes=configs.C5["budget_bytes"], max_slots=64, round_iters=20)
+    served = summarise(server.run(reqs, realtime=True))
+    rounds = server.rounds
+    server.close()
+    plain = summarise(serve_sequential(reqs, realtime=True))
+    return {"requests": n_jobs, "arrival_rate_per_s": rate, "load_vs_sequential_capacity": load,
+            "sequential_capacity_per_s": cap,
+            "workload": "Poisson stream; 128..512^2, 90..720 views, parallel/fan 50/50, 1..4 windows, 16..64 "
+                        "energies, tol 1e-3, HBM budget 150 GB, 20 iterations per round",
+            "served": dict(served, rounds=rounds), "sequential": plain,
+            "speedup_recon_per_s": served["recon_per_s"] / plain["recon_per_s"],
+            "p99_latency_ratio": plain["p99_latency_s"] / served["p99_latency_s"]}
+
+
+def make_job_inputs(ex, torch, spec, dev, rank=0):
+    """Plan, counts, step size and ground truth of one synthetic job."""
+    plan, y, mu, S, xs = make_counts(ex, torch, spec, dev, rank)
+    normA, _ = plan.norm_estimate(max_iters=100, rtol=1e-6)
+    eta = plan.recommended_eta(spec["I0"], normA)
+    return plan, y, eta, xs
+
+
+def run_batched(ex, torch, dev, n_jobs: int, iters: int, rank: int):
+    """The batched mix: n_jobs reconstructions of uneven size/views/windows,
+    (a) one after another with exact_solve, (b) in one persistent launch with
+    exact_batch_solve, (c) the same batch replayed from a captured CUDA graph.
+    Returns reconstructions/s, latencies and mean PSNR of each."""
+    specs = configs.c4_jobs(n_jobs=n_jobs)
+    jobs_in = [make_job_inputs(ex, torch, sp, dev, rank) for sp in specs]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    xs_seq = [torch.zeros(p.shape_img, dtype=torch.float32, device=dev) for p, _, _, _ in jobs_in]
+
+    def seq_pass():
+        ends = []
+        for (p, y, eta, _), x, sp in zip(jobs_in, xs_seq, specs):
+            x.zero_()
+            p.solve(y, sp["I0"], eta, iters, x=x, sync=False)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+            ends.append(ev)
+        return ends
+
+    batch = ex.Batch(n_jobs)
+    xs_b = [torch.zeros(p.shape_img, dtype=torch.float32, device=dev) for p, _, _, _ in jobs_in]
+    bjobs = [ex.Job(plan=p, y=y, I0=sp["I0"], eta=eta, iters=iters, x=x)
+             for (p, y, eta, _), x, sp in zip(jobs_in, xs_b, specs)]
+
+    def batch_pass():
+        for x in xs_b:
+            x.zero_()
+        batch.solve(bjobs, sync=False)
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = fn()
+            b = torch.cuda.Event(enable_timing=True)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            lat = [a.elapsed_time(e) for e in out] if out else None
+            if best is None or ms < best[0]:
+                best = (ms, lat)
+        return best
+
+    def psnr_of(xs):
+        vals = []
+        for x, (_, _, _, truth) in zip(xs, jobs_in):
+            rmse = float(np.sqrt(np.mean((x.double().cpu().numpy() - truth) ** 2)))
+            vals.append(20 * math.log10(1.0 / rmse))
+        return float(np.mean(vals))
+
+    seq_ms, seq_lat = timed(seq_pass)
+    psnr_seq = psnr_of(xs_seq)
+    b_ms, _ = timed(batch_pass)
+    psnr_b = psnr_of(xs_b)
+    # graph capture of the whole batched call (zeroing the iterates included)
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream()
+    cs.wait_stream(stream)
+    with torch.cuda.stream(cs):
+        with torch.cuda.graph(g, stream=cs):
+            batch_pass()
+    torch.cuda.synchronize()
+    g_ms, _ = timed(lambda: g.replay())
+    psnr_g = psnr_of(xs_b)
+
+    seq_lat = sorted(seq_lat)
+    out = {"jobs": n_jobs, "iters_per_job": iters, "workload": "C4 mix: " + ", ".join(sorted(
+        {f"{sp['geometry']['nx']}^2" for sp in specs})) + "; parallel beam 60..360 views; 1..4 windows; 32 energies",
+        "sequential": {"recon_per_s": n_jobs / (seq_ms / 1e3), "ms": seq_ms,
+                       "p50_latency_ms": seq_lat[len(seq_lat) // 2], "p99_latency_ms": seq_lat[-1],
+                       "mean_psnr_db": psnr_seq},
+        "batched": {"recon_per_s": n_jobs / (b_ms / 1e3), "ms": b_ms, "p50_latency_ms": b_ms, "p99_latency_ms": b_ms,
+                    "mean_psnr_db": psnr_b},
+        "batched_graph": {"recon_per_s": n_jobs / (g_ms / 1e3), "ms": g_ms, "mean_psnr_db": psnr_g},
+        "speedup_vs_sequential": seq_ms / b_ms}
+    batch.close()
+    for p, _, _, _ in jobs_in:
+        p.close()
+    return out
+
+
 def run_exact(args):
     import torch
     import torch.distributed as dist
@@ -372,6 +544,10 @@ def run_exact(args):
             "clocks": clocks.summary(),
             "psnr_db": psnr, "eta": eta, "normA_sq": normA, "norm_estimate": {"ms": norm_ms, "iters": norm_iters},
             "plan_create_ms": plan_ms}
+    if not args.no_batched:
+        line["batched"] = run_batched(ex, torch, dev, args.batch_jobs, args.batch_iters or configs.C4["iters"], rank)
+    if not args.no_served:
+        line["served"] = run_served(ex, torch, dev, args.serve_jobs, args.serve_load, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_baseline_iters)
     if rank == 0:

@@ -181,9 +181,59 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
 exact_status exact_norm_estimate(exact_plan_t plan, int max_iters, double rtol, double *normA_sq,
                                  int *iters_done, exact_stream_t stream);
 
+/* The same power iteration with the FP32 projector kernels (FP64 norms and
+ * Rayleigh quotients): ~1e-6 relative agreement with exact_norm_estimate at a
+ * small fraction of its cost (FP64 arithmetic runs at a low rate on GB300);
+ * used where a step size is needed per request.  Synchronises.  Needs the
+ * workspace. */
+exact_status exact_norm_estimate_f32(exact_plan_t plan, int max_iters, double rtol, double *normA_sq,
+                                     int *iters_done, exact_stream_t stream);
+
 /* Step size 1/(4L) of Theorem 1 with L = I0 (normA_sq / m) sum_k mu_k sum_w S[w][k]
  * (the Lipschitz bound of Sec. 4.2, m = n_windows * n_rays).  Host arithmetic. */
 exact_status exact_recommended_eta(exact_plan_t plan, double I0, double normA_sq, double *eta);
+
+/* ---- Batched solves (many reconstructions in one persistent launch) ---- */
+
+typedef struct exact_batch *exact_batch_t;
+
+/* One reconstruction of a batch: a plan with its bound workspace (each job
+ * needs its own plan and workspace), device counts y as in exact_operator, the
+ * source intensity, the step, the iteration count, the options (average_tail
+ * must be 0), the device image x (x_1 in, result out) and an optional host
+ * info struct written when the stream reaches the end of the batch. */
+typedef struct {
+    exact_plan_t plan;
+    const void *y;
+    exact_dtype y_dtype;
+    double I0;
+    double eta;
+    int iters;
+    exact_solve_opts opts;
+    float *x;
+    exact_solve_info *info;
+} exact_job;
+
+/* Create a batch context for up to max_jobs (1..256) jobs per call: it owns a
+ * few small device buffers (job descriptors, tensor maps, link coefficients,
+ * work counters) and pinned host staging.  Synchronises. */
+exact_status exact_batch_create(int max_jobs, exact_batch_t *out);
+
+/* Free a batch context (no work using it may be in flight). */
+exact_status exact_batch_destroy(exact_batch_t batch);
+
+/* Run the projected extragradient iteration of every job in one persistent
+ * kernel launch: the work of all jobs (forward units, adjoint tiles,
+ * reductions of each iteration) is handed out in a fixed order through a
+ * device work counter; an item waits (bounded spin, then EXACT_ERR_TIMEOUT)
+ * only for the previous phase of its own job, so different jobs overlap.
+ * Per job the arithmetic is the same for any batch composition, so a job's
+ * result does not depend on the other jobs.  Jobs on one call must be
+ * distinct plans on the current device.  Asynchronous on `stream` (set-up
+ * kernels, one persistent launch, result copies); capturable in a CUDA graph.
+ * The context's staging is reused by the next call, which waits for this call's
+ * staging copy first. */
+exact_status exact_batch_solve(exact_batch_t batch, const exact_job *jobs, int n_jobs, exact_stream_t stream);
 
 /* Number of nonzero entries of A (pairs of ray and pixel with a positive
  * Joseph weight), counted in FP64 on the host at plan creation: the

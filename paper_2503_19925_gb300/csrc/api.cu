@@ -325,24 +325,52 @@ size_t carve(Plan &P, char *base)
     const int nb_adj = adjoint_blocks(P.g.nx, P.g.ny);
     const int nb_fwd = forward_d_blocks(P.n);
     const int nb_adj_d = adjoint_d_blocks(P.g.nx, P.g.ny);
-    P.partials = c.take<double>(base, (size_t)(2 * nb_adj + nb_fwd + nb_adj_d));
+    const int nb_d = nb_adj_d > kSumsqParts ? nb_adj_d : kSumsqParts;
+    P.partials = c.take<double>(base, (size_t)(2 * nb_adj + (nb_fwd > kSumsqParts ? nb_fwd : kSumsqParts) + nb_d));
     P.avg = c.take<double>(base, (size_t)P.d);
     P.xrd = c.take<double>(base, (size_t)(ny * P.ldr()));
     P.xcd = c.take<double>(base, (size_t)(nx * P.ldc()));
     P.zd = c.take<double>(base, (size_t)P.n);
+    P.w32 = c.take<float>(base, (size_t)P.d);
     P.state = c.take<DevState>(base, 1);
     return c.off;
 }
 
+// Host-function payload that copies a solve's device state (already copied
+// to pinned memory) into the caller's info struct.  A payload enqueued outside
+// stream capture runs once and frees itself; one captured in a CUDA graph runs
+// on every replay, so it stays alive and is freed with its owner.
+struct InfoCopy {
+    const DevState *src;
+    exact_solve_info *dst;
+    bool one_shot;
+};
+
 void info_copy_cb(void *data)
 {
-    auto *pair = static_cast<std::pair<const DevState *, exact_solve_info *> *>(data);
-    const DevState *s = pair->first;
-    exact_solve_info *dst = pair->second;
-    dst->iters_done = s->iters_done;
-    dst->rel_res = s->rel_res;
-    dst->status = (exact_status)s->status;
-    delete pair;
+    InfoCopy *c = static_cast<InfoCopy *>(data);
+    c->dst->iters_done = c->src->iters_done;
+    c->dst->rel_res = c->src->rel_res;
+    c->dst->status = (exact_status)c->src->status;
+    if (c->one_shot) delete c;
+}
+
+// Enqueue the copy of `st` (device) to `info` (host) on stream s.
+exact_status enqueue_info(DevState *st, DevState *host_state, exact_solve_info *info, std::vector<void *> &keep,
+                          cudaStream_t s)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    EXACT_TRY(cudaStreamIsCapturing(s, &cap));
+    EXACT_TRY(cudaMemcpyAsync(host_state, st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    InfoCopy *c = new (std::nothrow) InfoCopy{host_state, info, cap == cudaStreamCaptureStatusNone};
+    if (!c) return EXACT_ERR_OOM;
+    cudaError_t e = cudaLaunchHostFunc(s, info_copy_cb, c);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_status(e);
+    }
+    if (!c->one_shot) keep.push_back(c);
+    return EXACT_OK;
 }
 
 LinkCoef make_coef(const Plan &P, double I0)
@@ -580,6 +608,7 @@ exact_status exact_plan_destroy(exact_plan_t plan)
     if (P->views) cudaFree(P->views);
     if (P->host_state) cudaFreeHost(P->host_state);
     if (P->prof_ev) prof_free(*P);
+    for (void *c : P->captured_infos) delete static_cast<InfoCopy *>(c);
     if (prev >= 0 && prev != P->device) cudaSetDevice(prev);
     delete P;
     return EXACT_OK;
@@ -809,14 +838,8 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     EXACT_TRY(launch_unpack(P.xr[0], P.ldr(), P.g.nx, P.g.ny, x, o.average_tail ? P.avg : nullptr, P.state,
                             avg_from, s));
     if (info) {
-        EXACT_TRY(cudaMemcpyAsync(P.host_state, P.state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-        auto *pair = new (std::nothrow) std::pair<const DevState *, exact_solve_info *>(P.host_state, info);
-        if (!pair) return EXACT_ERR_OOM;
-        cudaError_t e = cudaLaunchHostFunc(s, info_copy_cb, pair);
-        if (e != cudaSuccess) {
-            delete pair;
-            return cuda_status(e);
-        }
+        st = enqueue_info(P.state, P.host_state, info, P.captured_infos, s);
+        if (st != EXACT_OK) return st;
     }
     return EXACT_OK;
 }
@@ -845,6 +868,67 @@ exact_status exact_norm_estimate(exact_plan_t plan, int max_iters, double rtol, 
             EXACT_TRY(launch_adjoint_d(P.rays_d, P.views, P.g.n_views, P.g.n_bins, P.g.nx, P.g.ny, P.zd, P.xrd,
                                        P.xcd, P.ldr(), P.ldc(), pw, P.state, fan, s));
             EXACT_TRY(launch_power_reduce(pz, nb_fwd, pw, nb_adj_d, P.state, it, rtol, s));
+        }
+        EXACT_TRY(cudaMemcpyAsync(P.host_state, P.state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        EXACT_TRY(cudaStreamSynchronize(s));
+        if (P.host_state->done) break;
+    }
+    if (P.host_state->status != EXACT_OK) return (exact_status)P.host_state->status;
+    *normA_sq = P.host_state->lam;
+    if (iters_done) *iters_done = P.host_state->iters_done;
+    return EXACT_OK;
+}
+
+exact_status exact_norm_estimate_f32(exact_plan_t plan, int max_iters, double rtol, double *normA_sq,
+                                     int *iters_done, exact_stream_t stream)
+{
+    exact_status st = check_plan(plan, true);
+    if (st != EXACT_OK) return st;
+    if (!normA_sq || max_iters < 1 || !isfin(rtol) || rtol < 0.0) return EXACT_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int nb_adj = adjoint_blocks(P.g.nx, P.g.ny);
+    double *pz = P.partials + 2 * nb_adj;
+    double *pw = pz + (forward_d_blocks(P.n) > kSumsqParts ? forward_d_blocks(P.n) : kSumsqParts);
+    EXACT_TRY(launch_power_init_f(P.w32, P.d, P.state, s));
+    FwdArgs f;
+    memset(&f, 0, sizeof(f));
+    f.img = img_of(P, 0);
+    f.rays = P.rays_f;
+    f.bits = P.ray_bits;
+    f.delta = P.ray_delta;
+    f.units = P.units;
+    f.kstart = P.kstart;
+    f.n_units = P.n_units;
+    f.err = P.state;
+    f.state = P.state;
+    f.n = P.n;
+    f.z = P.r;
+    AdjArgs a;
+    memset(&a, 0, sizeof(a));
+    a.rays = P.rays_f;
+    a.views = P.views;
+    a.n_views = P.g.n_views;
+    a.n_bins = P.g.n_bins;
+    a.nx = P.g.nx;
+    a.ny = P.g.ny;
+    a.r = P.r;
+    a.delta = P.ray_delta;
+    a.scale = 1.0f;
+    a.out = P.w32;
+    a.state = P.state;
+    const int chunk = 8;
+    for (int it0 = 0; it0 < max_iters; it0 += chunk) {
+        const int it1 = it0 + chunk < max_iters ? it0 + chunk : max_iters;
+        for (int it = it0; it < it1; ++it) {
+            // v_k = w_k / ||w_k|| into the padded copies, z = A v_k, w_{k+1} = A^T z
+            EXACT_TRY(launch_pack(P.w32, P.xr[0], P.xc[0], P.g.nx, P.g.ny, P.ldr(), P.ldc(), 0.f, 0.f, false, s,
+                                  &P.state->inv_norm));
+            EXACT_TRY(launch_forward(f, false, nullptr, P.maps_r[0], P.maps_c[0], s));
+            EXACT_TRY(launch_sumsq(P.r, P.n, pz, kSumsqParts, s));
+            EXACT_TRY(launch_adjoint(a, ADJ_PLAIN, P.g.beam == 1, s));
+            EXACT_TRY(launch_sumsq(P.w32, P.d, pw, kSumsqParts, s));
+            EXACT_TRY(launch_power_reduce(pz, kSumsqParts, pw, kSumsqParts, P.state, it, rtol, s));
         }
         EXACT_TRY(cudaMemcpyAsync(P.host_state, P.state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
         EXACT_TRY(cudaStreamSynchronize(s));
@@ -925,6 +1009,238 @@ exact_status exact_profile_read(exact_plan_t plan, double *ms, long long *launch
     for (int k = 0; k < EXACT_PROF_KINDS; ++k) {
         if (ms) ms[k] = acc[k];
         if (launches) launches[k] = cnt[k];
+    }
+    return EXACT_OK;
+}
+
+}  // extern "C"
+
+// ================================================================ batches
+
+namespace {
+
+// Host staging and its device mirror share this layout (one copy per call).
+struct BatchLayout {
+    size_t jobs, maps, coefs, prefix, total;
+};
+
+BatchLayout batch_layout(int max_jobs)
+{
+    BatchLayout L;
+    size_t off = 0;
+    L.jobs = off;
+    off = align_up(off + sizeof(BatchJob) * (size_t)max_jobs);
+    L.maps = off;
+    off = align_up(off + sizeof(CUtensorMap) * 4 * (size_t)max_jobs);
+    L.coefs = off;
+    off = align_up(off + sizeof(LinkCoef) * (size_t)max_jobs);
+    L.prefix = off;
+    off = align_up(off + sizeof(int) * (5 * (size_t)max_jobs + 1));
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct exact_batch {
+    int device = -1;
+    int max_jobs = 0;
+    BatchLayout L;
+    char *host = nullptr;   // pinned staging
+    char *dev = nullptr;    // device mirror
+    unsigned long long *next = nullptr;
+    unsigned *done_items = nullptr;
+    int *abort_flag = nullptr;
+    char *counters = nullptr;
+    size_t counter_bytes = 0;
+    cudaEvent_t staged = nullptr;
+    bool staged_pending = false;
+    int grid = 0;
+    std::vector<void *> captured_infos;  // info payloads of captured graphs
+};
+
+extern "C" {
+
+exact_status exact_batch_create(int max_jobs, exact_batch_t *out)
+{
+    if (!out) return EXACT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (max_jobs < 1 || max_jobs > kMaxBatch) return EXACT_ERR_INVALID_ARG;
+    exact_batch *B = new (std::nothrow) exact_batch();
+    if (!B) return EXACT_ERR_OOM;
+    if (cudaGetDevice(&B->device) != cudaSuccess) {
+        delete B;
+        return EXACT_ERR_CUDA;
+    }
+    B->max_jobs = max_jobs;
+    B->L = batch_layout(max_jobs);
+    B->counter_bytes = align_up(sizeof(unsigned long long)) + align_up(sizeof(unsigned) * (size_t)max_jobs) +
+                       align_up(sizeof(int));
+    cudaError_t e = cudaMallocHost(&B->host, B->L.total);
+    if (e == cudaSuccess) e = cudaMalloc(&B->dev, B->L.total);
+    if (e == cudaSuccess) e = cudaMalloc(&B->counters, B->counter_bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->staged, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        exact_batch_destroy(B);
+        return cuda_status(e);
+    }
+    memset(B->host, 0, B->L.total);
+    B->next = reinterpret_cast<unsigned long long *>(B->counters);
+    B->done_items = reinterpret_cast<unsigned *>(B->counters + align_up(sizeof(unsigned long long)));
+    B->abort_flag = reinterpret_cast<int *>(B->counters + align_up(sizeof(unsigned long long)) +
+                                            align_up(sizeof(unsigned) * (size_t)max_jobs));
+    B->grid = batch_grid_size();
+    *out = B;
+    return EXACT_OK;
+}
+
+exact_status exact_batch_destroy(exact_batch_t B)
+{
+    if (!B) return EXACT_OK;
+    if (B->staged) cudaEventDestroy(B->staged);
+    for (void *c : B->captured_infos) delete static_cast<InfoCopy *>(c);
+    if (B->host) cudaFreeHost(B->host);
+    if (B->dev) cudaFree(B->dev);
+    if (B->counters) cudaFree(B->counters);
+    delete B;
+    return EXACT_OK;
+}
+
+exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_jobs, exact_stream_t stream)
+{
+    if (!B || !jobs || n_jobs < 1 || n_jobs > B->max_jobs) return EXACT_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return EXACT_ERR_CUDA;
+    if (dev != B->device) return EXACT_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int rounds = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const exact_job &J = jobs[j];
+        exact_status st = check_plan(J.plan, true);
+        if (st != EXACT_OK) return st;
+        if (!J.y || !J.x) return EXACT_ERR_INVALID_ARG;
+        if (J.y_dtype != EXACT_F32 && J.y_dtype != EXACT_BF16) return EXACT_ERR_INVALID_ARG;
+        if (!isfin(J.I0) || !(J.I0 > 0.0) || !isfin(J.eta) || !(J.eta > 0.0) || J.iters < 0)
+            return EXACT_ERR_INVALID_ARG;
+        const exact_solve_opts &o = J.opts;
+        if (isnan(o.lo) || isnan(o.hi) || o.lo > o.hi || o.lo == INFINITY || o.hi == -INFINITY)
+            return EXACT_ERR_INVALID_ARG;
+        if (!isfin(o.tol) || o.tol < 0.0 || o.check_every < 0) return EXACT_ERR_INVALID_ARG;
+        if (o.average_tail) return EXACT_ERR_UNSUPPORTED;
+        for (int q = 0; q < j; ++q)
+            if (jobs[q].plan == J.plan) return EXACT_ERR_INVALID_ARG;
+        rounds = J.iters > rounds ? J.iters : rounds;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    EXACT_TRY(cudaStreamIsCapturing(s, &cap));
+    // the previous call's staging copy must have left the host buffer
+    if (B->staged_pending && cap == cudaStreamCaptureStatusNone) {
+        EXACT_TRY(cudaEventSynchronize(B->staged));
+        B->staged_pending = false;
+    }
+
+    BatchJob *hj = reinterpret_cast<BatchJob *>(B->host + B->L.jobs);
+    CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(B->host + B->L.maps);
+    LinkCoef *hc = reinterpret_cast<LinkCoef *>(B->host + B->L.coefs);
+    int *hp = reinterpret_cast<int *>(B->host + B->L.prefix);
+    const CUtensorMap *dm = reinterpret_cast<const CUtensorMap *>(B->dev + B->L.maps);
+    const LinkCoef *dc = reinterpret_cast<const LinkCoef *>(B->dev + B->L.coefs);
+    for (int j = 0; j < n_jobs; ++j) {
+        const exact_job &Jb = jobs[j];
+        Plan &P = *reinterpret_cast<Plan *>(Jb.plan);
+        BatchJob &J = hj[j];
+        memset(&J, 0, sizeof(J));
+        J.img[0] = img_of(P, 0);
+        J.img[1] = img_of(P, 1);
+        for (int q = 0; q < 2; ++q) {
+            J.xr[q] = P.xr[q];
+            J.xc[q] = P.xc[q];
+        }
+        hm[4 * j + 0] = P.maps_r[0];
+        hm[4 * j + 1] = P.maps_c[0];
+        hm[4 * j + 2] = P.maps_r[1];
+        hm[4 * j + 3] = P.maps_c[1];
+        J.maps = dm + 4 * j;
+        hc[j] = make_coef(P, Jb.I0);
+        J.coef = dc + j;
+        J.state = P.state;
+        J.f.rays = P.rays_f;
+        J.f.bits = P.ray_bits;
+        J.f.delta = P.ray_delta;
+        J.f.units = P.units;
+        J.f.kstart = P.kstart;
+        J.f.n_units = P.n_units;
+        J.f.err = P.state;
+        J.f.n = P.n;
+        J.f.Y = P.Y;
+        J.f.r = P.r;
+        J.f.K = P.K;
+        J.a.rays = P.rays_f;
+        J.a.views = P.views;
+        J.a.n_views = P.g.n_views;
+        J.a.n_bins = P.g.n_bins;
+        J.a.nx = P.g.nx;
+        J.a.ny = P.g.ny;
+        J.a.r = P.r;
+        J.a.scale = (float)(-Jb.eta / ((double)P.W * (double)P.n));
+        J.a.base_r = P.xr[0];
+        J.a.ldr = P.ldr();
+        J.a.ldc = P.ldc();
+        J.a.lo = (float)Jb.opts.lo;
+        J.a.hi = (float)Jb.opts.hi;
+        J.a.partials = P.partials;
+        J.a.state = P.state;
+        J.n_units = P.n_units;
+        J.tiles_x = (P.g.nx + 31) / 32;
+        J.tiles_y = (P.g.ny + 7) / 8;
+        J.fan = P.g.beam == 1;
+        J.iters = Jb.iters;
+        J.check_every = Jb.opts.check_every;
+        J.tol = Jb.opts.tol;
+        const int T = J.tiles_x * J.tiles_y, U = P.n_units;
+        const int per[5] = {U, T, U, T, 1};
+        J.phase_off[0] = 0;
+        for (int p = 0; p < 5; ++p) J.phase_off[p + 1] = J.phase_off[p] + per[p];
+    }
+    long long run = 0;
+    for (int p = 0; p < 5; ++p)
+        for (int j = 0; j < n_jobs; ++j) {
+            hp[p * n_jobs + j] = (int)run;
+            run += hj[j].phase_off[p + 1] - hj[j].phase_off[p];
+        }
+    if (run >= (1LL << 31)) return EXACT_ERR_UNSUPPORTED;
+    hp[5 * n_jobs] = (int)run;
+    for (int j = 0; j < n_jobs; ++j)
+        if ((unsigned long long)hj[j].phase_off[5] * (unsigned long long)(rounds + 1) >= (1ULL << 32))
+            return EXACT_ERR_UNSUPPORTED;
+
+    EXACT_TRY(cudaMemcpyAsync(B->dev, B->host, B->L.total, cudaMemcpyHostToDevice, s));
+    if (cap == cudaStreamCaptureStatusNone) {
+        EXACT_TRY(cudaEventRecord(B->staged, s));
+        B->staged_pending = true;
+    }
+    EXACT_TRY(cudaMemsetAsync(B->counters, 0, B->counter_bytes, s));
+    for (int j = 0; j < n_jobs; ++j) {
+        const exact_job &Jb = jobs[j];
+        Plan &P = *reinterpret_cast<Plan *>(Jb.plan);
+        EXACT_TRY(launch_reset_state(P.state, s));
+        EXACT_TRY(launch_collapse(Jb.y, Jb.y_dtype, P.W, P.n, P.Y, s));
+        EXACT_TRY(launch_pack(Jb.x, P.xr[0], P.xc[0], P.g.nx, P.g.ny, P.ldr(), P.ldc(), (float)Jb.opts.lo,
+                              (float)Jb.opts.hi, true, s));
+        EXACT_TRY(cudaMemsetAsync(P.xr[1], 0, sizeof(float) * (size_t)(P.g.ny * P.ldr()), s));
+        EXACT_TRY(cudaMemsetAsync(P.xc[1], 0, sizeof(float) * (size_t)(P.g.nx * P.ldc()), s));
+    }
+    EXACT_TRY(launch_batch(reinterpret_cast<const BatchJob *>(B->dev + B->L.jobs), n_jobs,
+                           reinterpret_cast<const int *>(B->dev + B->L.prefix), rounds, B->next, B->done_items,
+                           B->abort_flag, B->grid, s));
+    for (int j = 0; j < n_jobs; ++j) {
+        const exact_job &Jb = jobs[j];
+        Plan &P = *reinterpret_cast<Plan *>(Jb.plan);
+        EXACT_TRY(launch_unpack(P.xr[0], P.ldr(), P.g.nx, P.g.ny, Jb.x, nullptr, P.state, 0, s));
+        if (Jb.info) {
+            exact_status st = enqueue_info(P.state, P.host_state, Jb.info, B->captured_infos, s);
+            if (st != EXACT_OK) return st;
+        }
     }
     return EXACT_OK;
 }

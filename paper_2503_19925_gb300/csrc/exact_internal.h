@@ -6,6 +6,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/exact.h"
 
 namespace exact {
@@ -106,6 +108,7 @@ struct Plan {
     double *avg = nullptr;               // tail-average accumulator [d]
     double *xrd = nullptr, *xcd = nullptr;  // FP64 padded copies (power iteration)
     double *zd = nullptr;                // FP64 projections [n]
+    float *w32 = nullptr;                // FP32 power-iteration image [d]
     DevState *state = nullptr;
     // pinned host mirror of the device state (solve info)
     DevState *host_state = nullptr;
@@ -115,7 +118,7 @@ struct Plan {
     int n_units = 0;
     // tensor maps of the padded copies: maps_r[q] over xr[q], maps_c[q] over xc[q]
     CUtensorMap maps_r[2], maps_c[2];
-    bool maps_ok = false;
+    std::vector<void *> captured_infos;  // solve-info payloads owned by captured graphs
     // kernel timing (profiling aid): event pairs recorded around sampled launches
     int prof_every = 0;
     int prof_used = 0;              // event pairs recorded since the last read
@@ -182,6 +185,27 @@ struct AdjArgs {
     const DevState *state;
 };
 
+// One job of the persistent multi-job kernel (k_batch.cu).  A round of a job
+// is one extragradient iteration: phase 0 forward+link on x_t (n_units items),
+// 1 adjoint half step (n_tiles items), 2 forward+link on x_{t+1/2}, 3 adjoint
+// full step, 4 reduction (1 item).
+struct BatchJob {
+    FwdArgs f;                 // img is set per phase
+    AdjArgs a;                 // out_r/out_c/iter set per phase
+    ImgF img[2];
+    float *xr[2], *xc[2];
+    const CUtensorMap *maps;   // [4] in global memory: rows 0, cols 0, rows 1, cols 1
+    const LinkCoef *coef;      // global memory
+    DevState *state;
+    int n_units, tiles_x, tiles_y, fan;
+    int iters, check_every;
+    double tol;
+    int phase_off[6];          // items of the job before phase p within a round; [5] = items per round
+};
+
+constexpr int kBatchThreads = 128;  // = kFR, and 4 adjoint warps
+constexpr int kMaxBatch = 256;      // jobs per batch launch
+
 // ---- launchers (each returns cudaGetLastError()) ------------------------------
 cudaError_t launch_forward(const FwdArgs &a, bool link, const LinkCoef *coef, const CUtensorMap &map_r,
                            const CUtensorMap &map_c, cudaStream_t s);
@@ -190,7 +214,10 @@ int adjoint_blocks(int nx, int ny);    // blocks (= partial-norm pairs) of the F
 int adjoint_d_blocks(int nx, int ny);  // blocks (= partial sums) of the FP64 adjoint
 
 cudaError_t launch_pack(const float *x, float *xr, float *xc, int nx, int ny, long long ldr, long long ldc,
-                        float lo, float hi, bool project, cudaStream_t s);
+                        float lo, float hi, bool project, cudaStream_t s, const double *scale = nullptr);
+constexpr int kSumsqParts = 256;  // fixed partial count of the FP32 sums of squares
+cudaError_t launch_sumsq(const float *v, long long n, double *partials, int nparts, cudaStream_t s);
+cudaError_t launch_power_init_f(float *w, long long d, DevState *st, cudaStream_t s);
 cudaError_t launch_unpack(const float *xr, long long ldr, int nx, int ny, float *x, const double *avg,
                           const DevState *state, int avg_from, cudaStream_t s);
 cudaError_t launch_collapse(const void *y, int dtype, int W, long long n, float *Y, cudaStream_t s);
@@ -208,6 +235,14 @@ int forward_d_blocks(long long n);
 cudaError_t launch_adjoint_d(const RayD *rays, const ViewRec *views, int n_views, int n_bins, int nx, int ny,
                              const double *zd, double *xrd, double *xcd, long long ldr, long long ldc,
                              double *partials, DevState *st, bool fan, cudaStream_t s);
+// Persistent multi-job kernel: jobs[n_jobs] in device memory, prefix[5 n_jobs + 1]
+// = items of the (phase, job) segments before each segment within a round
+// (phase-major), rounds = largest iteration count.  next/done_items/abort are
+// zeroed by the caller.
+cudaError_t launch_batch(const BatchJob *jobs, int n_jobs, const int *prefix, int rounds, unsigned long long *next,
+                         unsigned *done_items, int *abort_flag, int grid, cudaStream_t s);
+int batch_grid_size();
+
 cudaError_t launch_power_reduce(const double *pz, int nz, const double *pw, int nw, DevState *st, int iter,
                                 double rtol, cudaStream_t s);
 

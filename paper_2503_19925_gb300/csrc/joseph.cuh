@@ -1,0 +1,352 @@
+// joseph.cuh -- device bodies of the Joseph projector work items, shared by
+// the per-plan kernels (k_forward.cu, k_adjoint.cu) and the persistent
+// multi-job kernel (k_batch.cu).
+//
+//   forward_unit: Joseph forward walk of one work unit (up to kFR adjacent rays
+//     of one view), image bands staged in shared memory by 2D tensor-map
+//     copies, optional link/residual epilogue (Eq. (7), Eq. (8));
+//   adjoint_tile: deterministic gather of A^T r over one kTW x kTH pixel tile
+//     (strip walk), with the extragradient epilogue of Eq. (11) and the FP64
+//     partial norms of the stopping rule.
+//
+// COHERENT selects loads that bypass the non-coherent L1 paths for data that
+// other CTAs rewrite during the same launch (the persistent kernel).
+#pragma once
+
+#include "exact_internal.h"
+
+namespace exact {
+
+// ------------------------------------------------------------------ helpers
+
+constexpr unsigned kBoxBytes = kFC * kFHB * sizeof(float);
+constexpr int kWaitSpins = 1 << 20;  // bounded mbarrier wait (try_wait also suspends briefly)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for the given phase parity; true when the phase completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t addr = smem_u32(bar);
+    for (int it = 0; it < kWaitSpins; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// One kFC x kFHB box of the tensor map at (x = padded cross index, y = line).
+__device__ __forceinline__ void tma_box(float *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    const uint32_t b = smem_u32(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(kBoxBytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(b)
+        : "memory");
+}
+
+template <bool COHERENT>
+__device__ __forceinline__ float ld_dyn(const float *p)
+{
+    return COHERENT ? __ldcg(p) : __ldg(p);
+}
+
+// Shared memory of one forward item (the two staging buffers); the two
+// mbarriers and the broadcast flag live outside so that a persistent kernel can
+// reuse this space for other items.
+struct FwdSmem {
+    float buf[2][kFC * kFHB];
+};
+
+// ------------------------------------------------------------------ forward
+
+// Joseph forward walk of work unit `ui` (see k_forward.cu for the design).
+// Thread 0 owns the two mbarriers; ph[b] counts the completed phases of
+// barrier b across calls (both start at 0 after mbar_init).  Returns false
+// (uniformly) if a staging copy timed out; the caller must then stop using the
+// shared buffers.
+template <bool LINK, bool COHERENT>
+__device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUtensorMap *map_r,
+                                             const CUtensorMap *map_c, const LinkCoef *coef, FwdSmem &sm,
+                                             uint64_t *bar, int *s_ok, uint32_t (&ph)[2])
+{
+    const FwdUnit u = a.units[ui];
+    const int t = threadIdx.x;
+    const bool has_ray = t < u.count;
+    const long long i = (long long)u.ray0 + t;
+    RayF rec = {0.f, 0.f, 0.f, 0.f};
+    int bits = 1;  // empty driving range (j_lo = 1 > j_hi = 0)
+    if (has_ray) {
+        rec = a.rays[i];
+        bits = a.bits[i];
+    }
+    const int jlo = ray_jlo(bits), jhi = ray_jhi(bits);
+    const CUtensorMap *map = u.axis ? map_r : map_c;
+    const int A = (int)rec.A;
+    const int *kst = a.kstart + u.koff;
+
+    if (t == 0 && u.nchunks > 0) {
+        // order earlier generic accesses of the buffers (and of global data
+        // synchronised with other CTAs) before the async-proxy copy
+        asm volatile("fence.proxy.async;" ::: "memory");
+        tma_box(sm.buf[0], map, kst[0] + kPad, u.jc0 * kFC, &bar[0]);
+    }
+    float acc = 0.0f;
+    for (int c = 0; c < u.nchunks; ++c) {
+        const int b = c & 1;
+        if (t == 0) {
+            const bool ok = mbar_wait(&bar[b], ph[b] & 1u);
+            if (ok) ph[b] += 1;
+            *s_ok = ok ? 1 : 0;
+            if (ok && c + 1 < u.nchunks) {
+                // the other buffer was last read before the barrier that ended
+                // chunk c - 1; order those reads before the async-proxy write
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_box(sm.buf[b ^ 1], map, kst[c + 1] + kPad, (u.jc0 + c + 1) * kFC, &bar[b ^ 1]);
+            }
+        }
+        __syncthreads();
+        if (!*s_ok) {
+            // the copy of chunk c never completed: report, wait (bounded) for
+            // it once more so no copy lands after the buffers are released
+            if (t == 0) {
+                mbar_wait(&bar[b], ph[b] & 1u);
+                if (a.err) {
+                    a.err->status = EXACT_ERR_TIMEOUT;
+                    a.err->done = 1;
+                }
+            }
+            return false;
+        }
+        const int j0 = (u.jc0 + c) * kFC;
+        const int ja = max(jlo, j0), jb = min(jhi, j0 + kFC - 1);
+        if (ja <= jb) {
+            // anchor: t(j0) = K + tau0 with tau0 accurate to FP32 rounding at ~1
+            const float jf = (float)j0;
+            const float p = rec.bh * jf;
+            const float e = fmaf(rec.bh, jf, -p);
+            const float P = floorf(p);
+            const float tau0 = ((p - P) + rec.a) + fmaf(rec.bl, jf, e);
+            // local row = K + floor(tau) - kstart, with the bias of the
+            // float-to-int floor folded in
+            const int off = A + (int)P - kst[c] - kFloorBias;
+            const float *sb = sm.buf[b] + (ja - j0) * kFHB;
+            float di = (float)(ja - j0);
+#pragma unroll 4
+            for (int j = ja; j <= jb; ++j) {
+                const float tau = fmaf(rec.bh, di, tau0);
+                // floor(tau) for |tau| < 2^22: a round-down add of 1.5 * 2^23
+                // leaves floor(tau) in the low mantissa bits
+                const float r = __fadd_rd(tau, kFloorMagic);
+                const float f = tau - (r - kFloorMagic);
+                // the host sized the band with a row of margin; the clamp only
+                // keeps a damaged table inside the buffer
+                const int row = min(max(off + __float_as_int(r), 0), kFHB - 2);
+                const float a0 = sb[row], a1 = sb[row + 1];
+                acc += fmaf(f, a1 - a0, a0);
+                sb += kFHB;
+                di += 1.0f;
+            }
+        }
+        __syncthreads();
+    }
+    if (!has_ray) return true;
+    const float delta = a.delta[i];
+    const float z = delta * acc;
+    if (!LINK) {
+        a.z[i] = z;
+        return true;
+    }
+    const float zp = fmaxf(z, 0.0f);
+    float lam = 0.0f;
+    for (int k = 0; k < a.K; ++k) lam = fmaf(coef->c[k], exp2f(-coef->mu2[k] * zp), lam);
+    a.r[i] = delta * (a.Y[i] - lam);
+    return true;
+}
+
+// ------------------------------------------------------------------ adjoint
+
+constexpr int kTW = 32;         // tile width (pixels) = lanes of a warp
+constexpr int kTH = 8;          // tile height = strip length of both walks
+constexpr int kRows = kTH + 2;  // accumulator rows: strip offsets -1 .. kTH
+static_assert(kTW % kTH == 0, "y-driven lanes split a tile row into whole segments");
+constexpr float kBinEps = 0.01f;
+
+template <int G>
+struct AdjSmem {
+    float acc[G][2][kRows * kTW];  // per warp: x-driven then y-driven accumulators
+    float stage[kTH][kTW + 1];
+    float tile[kTH][kTW + 1];
+    double red0[G], red1[G];
+};
+
+// Bin range of the rays that cross the segment between two points whose
+// detector projections are (num1/den1, num2/den2) + c, within [lo_bin, hi_bin).
+template <bool FAN>
+__device__ __forceinline__ void seg_range(float num1, float den1, float num2, float den2, float c, int lo_bin,
+                                          int hi_bin, int &b0, int &b1)
+{
+    const float u1 = FAN ? __fdividef(num1, den1) : num1;
+    const float u2 = FAN ? __fdividef(num2, den2) : num2;
+    float lo = fminf(u1, u2) + c - kBinEps;
+    float hi = fmaxf(u1, u2) + c + kBinEps;
+    lo = fminf(fmaxf(lo, -1.0f), (float)hi_bin);
+    hi = fminf(fmaxf(hi, -1.0f), (float)hi_bin);
+    b0 = max(lo_bin, (int)ceilf(lo));
+    b1 = min(hi_bin - 1, (int)floorf(hi));
+}
+
+// Walk rays b0..b1 of one view at driving index jf; deposit into acc rows
+// k + 1 and k + 2 (strip offset k = floor(t - kbase) in [-1, kTH - 1]).
+template <bool DELTA, bool COHERENT>
+__device__ __forceinline__ void strip_walk(const RayF *__restrict__ vrays, const float *__restrict__ vres,
+                                           const float *__restrict__ vdelta, int b0, int b1, float jf, float kbase,
+                                           float *__restrict__ acc, int lane)
+{
+    for (int b = b0; b <= b1; ++b) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(vrays + b));
+        const RayF rec = {q.x, q.y, q.z, q.w};
+        float rv = ld_dyn<COHERENT>(vres + b);
+        if (DELTA) rv *= __ldg(vdelta + b);
+        const float p = rec.bh * jf;
+        const float e = fmaf(rec.bh, jf, -p);
+        const float u = ((rec.A - kbase) + p) + (rec.a + fmaf(rec.bl, jf, e));
+        // floor(u) without the conversion pipe (|u| < 2^22)
+        const float r = __fadd_rd(u, kFloorMagic);
+        const float f = u - (r - kFloorMagic);
+        const int k = __float_as_int(r) - kFloorBias;
+        if (k >= -1 && k < kTH) {
+            const float w1 = f * rv;
+            acc[(k + 1) * kTW + lane] += rv - w1;
+            acc[(k + 2) * kTW + lane] += w1;
+        }
+    }
+}
+
+// A^T r over tile (bx, by) with the epilogue of MODE (see k_adjoint.cu).
+// blk is the tile's index for the partial norms.  Uses G warps.
+template <int MODE, bool FAN, bool DELTA, int G, bool COHERENT>
+__device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, long long blk, AdjSmem<G> &sm)
+{
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    float *accx = sm.acc[g][0];
+    float *accy = sm.acc[g][1];
+    for (int r = 0; r < kRows; ++r) {
+        accx[r * kTW + lane] = 0.0f;
+        accy[r * kTW + lane] = 0.0f;
+    }
+    const int tx0 = bx * kTW, ty0 = by * kTH;
+    // x-driven strip of this lane: column cx, rows ty0 .. ty0 + kTH - 1
+    const int cx = tx0 + lane;
+    const bool xok = cx < a.nx;
+    // strip end points, kept within one pixel of the image so that their
+    // fan-beam projections stay well defined (the source is outside the image)
+    const float fcx = (float)cx, fy_lo = (float)(ty0 - 1), fy_hi = (float)min(ty0 + kTH, a.ny);
+    // y-driven strip of this lane: row ry, columns cy0 .. cy0 + kTH - 1
+    const int ry = ty0 + (lane % kTH);
+    const int cy0 = tx0 + kTH * (lane / kTH);
+    const bool yok = ry < a.ny && cy0 < a.nx;
+    const float fry = (float)ry, fx_lo = (float)(cy0 - 1), fx_hi = (float)min(cy0 + kTH, a.nx);
+
+    for (int v = g; v < a.n_views; v += G) {
+        const ViewRec vr = a.views[v];
+        const long long vb = (long long)v * a.n_bins;
+        const RayF *vrays = a.rays + vb;
+        const float *vres = a.r + vb;
+        const float *vdel = DELTA ? a.delta + vb : nullptr;
+        if (vr.xb1 > vr.xb0 && xok) {
+            const float nb = fmaf(vr.n1, fcx, vr.n0), db = fmaf(vr.d1, fcx, vr.d0);
+            int b0, b1;
+            seg_range<FAN>(fmaf(vr.n2, fy_lo, nb), fmaf(vr.d2, fy_lo, db), fmaf(vr.n2, fy_hi, nb),
+                           fmaf(vr.d2, fy_hi, db), vr.c, vr.xb0, vr.xb1, b0, b1);
+            strip_walk<DELTA, COHERENT>(vrays, vres, vdel, b0, b1, fcx, (float)ty0, accx, lane);
+        }
+        if (vr.yb1 > vr.yb0 && yok) {
+            const float nb = fmaf(vr.n2, fry, vr.n0), db = fmaf(vr.d2, fry, vr.d0);
+            int b0, b1;
+            seg_range<FAN>(fmaf(vr.n1, fx_lo, nb), fmaf(vr.d1, fx_lo, db), fmaf(vr.n1, fx_hi, nb),
+                           fmaf(vr.d1, fx_hi, db), vr.c, vr.yb0, vr.yb1, b0, b1);
+            strip_walk<DELTA, COHERENT>(vrays, vres, vdel, b0, b1, fry, (float)cy0, accy, lane);
+        }
+    }
+    __syncthreads();
+
+    // fixed-order reduction over the warps: the y-driven parts first, staged
+    // transposed (row stride kTW + 1), then the x-driven parts
+    for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
+        const int l = t % kTW, k = t / kTW;  // accy column l, strip offset k
+        float s = 0.0f;
+        for (int q = 0; q < G; ++q) s += sm.acc[q][1][(k + 1) * kTW + l];
+        sm.stage[l % kTH][kTH * (l / kTH) + k] = s;
+    }
+    __syncthreads();
+    double s0 = 0.0, s1 = 0.0;
+    for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
+        const int px = t % kTW, py = t / kTW;
+        float gsum = sm.stage[py][px];
+        for (int q = 0; q < G; ++q) gsum += sm.acc[q][0][(py + 1) * kTW + px];
+        const int kx = tx0 + px, ky = ty0 + py;
+        const bool inside = kx < a.nx && ky < a.ny;
+        if (MODE == ADJ_PLAIN) {
+            if (inside) a.out[(long long)ky * a.nx + kx] = a.scale * gsum;
+        } else {
+            const long long pr = (long long)ky * a.ldr + kx + kPad;
+            const float xb = inside ? ld_dyn<COHERENT>(a.base_r + pr) : 0.0f;
+            // projection onto [lo, hi] that keeps a NaN (so the stopping rule sees it)
+            const float step = fmaf(a.scale, gsum, xb);
+            const float xn = inside ? (step < a.lo ? a.lo : (step > a.hi ? a.hi : step)) : 0.0f;
+            if (inside) a.out_r[pr] = xn;
+            sm.tile[py][px] = xn;
+            if (MODE == ADJ_EG_FINAL && inside) {
+                if (a.avg && a.iter >= a.avg_from) a.avg[(long long)ky * a.nx + kx] += (double)xn;
+                const double dd = (double)xn - (double)xb;
+                s0 += dd * dd;
+                s1 += (double)xb * (double)xb;
+            }
+        }
+    }
+    if (MODE == ADJ_PLAIN) return;
+    __syncthreads();
+    // column-major copy: kTH consecutive ky per kx row
+    for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
+        const int col = t / kTH, row = t % kTH;
+        const int ox = tx0 + col, oy = ty0 + row;
+        if (ox < a.nx && oy < a.ny) a.out_c[(long long)ox * a.ldc + oy + kPad] = sm.tile[row][col];
+    }
+    if (MODE == ADJ_EG_FINAL) {
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_down_sync(0xffffffffu, s0, o);
+            s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        }
+        if (lane == 0) {
+            sm.red0[g] = s0;
+            sm.red1[g] = s1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t0 = 0.0, t1 = 0.0;
+            for (int q = 0; q < G; ++q) {
+                t0 += sm.red0[q];
+                t1 += sm.red1[q];
+            }
+            a.partials[2 * blk] = t0;
+            a.partials[2 * blk + 1] = t1;
+        }
+    }
+}
+
+}  // namespace exact

@@ -27,155 +27,32 @@
 // kernel parameter space (uniform access).  The residual leaves the kernel
 // already multiplied by the ray's step length, the factor every entry of the
 // ray's row of A carries.
-#include "exact_internal.h"
+//
+// The walk itself (forward_unit) is in joseph.cuh, shared with the persistent
+// multi-job kernel of k_batch.cu.
+#include "joseph.cuh"
 
 namespace exact {
 
 namespace {
 
-constexpr unsigned kBoxBytes = kFC * kFHB * sizeof(float);
-constexpr int kWaitSpins = 1 << 20;  // bounded mbarrier wait (try_wait also suspends briefly)
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Bounded wait for the given phase parity; true when the phase completed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    const uint32_t addr = smem_u32(bar);
-    for (int it = 0; it < kWaitSpins; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// One kFC x kFHB box of the tensor map at (x = padded cross index, y = line).
-__device__ __forceinline__ void tma_box(float *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
-{
-    const uint32_t b = smem_u32(bar);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(kBoxBytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(b)
-        : "memory");
-}
-
 template <bool LINK>
 __global__ void __launch_bounds__(kFR) k_forward_tma(FwdArgs a, const __grid_constant__ CUtensorMap map_r,
-                                                     const __grid_constant__ CUtensorMap map_c, const LinkCoef coef)
+                                                     const __grid_constant__ CUtensorMap map_c,
+                                                     const __grid_constant__ LinkCoef coef)
 {
     if (a.state && a.state->done) return;
-    __shared__ __align__(128) float buf[2][kFC * kFHB];
+    __shared__ __align__(128) FwdSmem sm;
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_ok;
-
-    const FwdUnit u = a.units[blockIdx.x];
-    const int t = threadIdx.x;
-    const bool has_ray = t < u.count;
-    const long long i = (long long)u.ray0 + t;
-    RayF rec = {0.f, 0.f, 0.f, 0.f};
-    int bits = 1;  // empty driving range (j_lo = 1 > j_hi = 0)
-    if (has_ray) {
-        rec = a.rays[i];
-        bits = a.bits[i];
-    }
-    const int jlo = ray_jlo(bits), jhi = ray_jhi(bits);
-    const CUtensorMap *map = u.axis ? &map_r : &map_c;
-    const int A = (int)rec.A;
-    const int *kst = a.kstart + u.koff;
-
-    if (t == 0) {
+    if (threadIdx.x == 0) {
         mbar_init(&bar[0]);
         mbar_init(&bar[1]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        if (u.nchunks > 0) tma_box(buf[0], map, kst[0] + kPad, u.jc0 * kFC, &bar[0]);
     }
     __syncthreads();
-
-    float acc = 0.0f;
-    for (int c = 0; c < u.nchunks; ++c) {
-        if (t == 0) {
-            const bool ok = mbar_wait(&bar[c & 1], (uint32_t)(c >> 1) & 1u);
-            s_ok = ok ? 1 : 0;
-            if (ok && c + 1 < u.nchunks) {
-                // the other buffer was last read before the barrier that ended
-                // chunk c - 1; order those reads before the async-proxy write
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                tma_box(buf[(c + 1) & 1], map, kst[c + 1] + kPad, (u.jc0 + c + 1) * kFC, &bar[(c + 1) & 1]);
-            }
-        }
-        __syncthreads();
-        if (!s_ok) {
-            // the copy of chunk c never completed: report, wait (bounded) for
-            // it once more so no copy lands after exit, and leave
-            if (t == 0) {
-                mbar_wait(&bar[c & 1], (uint32_t)(c >> 1) & 1u);
-                if (a.err) {
-                    a.err->status = EXACT_ERR_TIMEOUT;
-                    a.err->done = 1;
-                }
-            }
-            return;
-        }
-        const int j0 = (u.jc0 + c) * kFC;
-        const int ja = max(jlo, j0), jb = min(jhi, j0 + kFC - 1);
-        if (ja <= jb) {
-            // anchor: t(j0) = K + tau0 with tau0 accurate to FP32 rounding at ~1
-            const float jf = (float)j0;
-            const float p = rec.bh * jf;
-            const float e = fmaf(rec.bh, jf, -p);
-            const float P = floorf(p);
-            const float tau0 = ((p - P) + rec.a) + fmaf(rec.bl, jf, e);
-            // local row = K + floor(tau) - kstart, with the bias of the
-            // float-to-int floor folded in
-            const int off = A + (int)P - kst[c] - kFloorBias;
-            const float *sb = buf[c & 1] + (ja - j0) * kFHB;
-            float di = (float)(ja - j0);
-#pragma unroll 4
-            for (int j = ja; j <= jb; ++j) {
-                const float tau = fmaf(rec.bh, di, tau0);
-                // floor(tau) for |tau| < 2^22: a round-down add of 1.5 * 2^23
-                // leaves floor(tau) in the low mantissa bits
-                const float r = __fadd_rd(tau, kFloorMagic);
-                const float f = tau - (r - kFloorMagic);
-                // the host sized the band with a row of margin; the clamp only
-                // keeps a damaged table inside the buffer
-                const int row = min(max(off + __float_as_int(r), 0), kFHB - 2);
-                const float a0 = sb[row], a1 = sb[row + 1];
-                acc += fmaf(f, a1 - a0, a0);
-                sb += kFHB;
-                di += 1.0f;
-            }
-        }
-        __syncthreads();
-    }
-    if (!has_ray) return;
-    const float delta = a.delta[i];
-    const float z = delta * acc;
-    if (!LINK) {
-        a.z[i] = z;
-        return;
-    }
-    const float zp = fmaxf(z, 0.0f);
-    float lam = 0.0f;
-    for (int k = 0; k < a.K; ++k) lam = fmaf(coef.c[k], exp2f(-coef.mu2[k] * zp), lam);
-    a.r[i] = delta * (a.Y[i] - lam);
+    uint32_t ph[2] = {0u, 0u};
+    forward_unit<LINK, false>(a, blockIdx.x, &map_r, &map_c, &coef, sm, bar, &s_ok, ph);
 }
 
 // FP64 forward of the power iteration: z = inv_norm * A w, plus per-block

@@ -15,29 +15,32 @@ __device__ __forceinline__ float proj(float v, float lo, float hi, bool project)
     return project ? (v < lo ? lo : (v > hi ? hi : v)) : v;
 }
 
-// Row-major copy with kPad zero columns on each side.
+// Row-major copy with kPad zero columns on each side (values times *scale
+// when scale is given).
 __global__ void k_pack_rows(const float *x, float *xr, int nx, int ny, long long ldr, float lo, float hi,
-                            bool project)
+                            bool project, const double *scale)
 {
     const long long total = (long long)ny * ldr;
+    const float sc = scale ? (float)*scale : 1.0f;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         const long long j = e / ldr;
         const long long k = e - j * ldr - kPad;
-        xr[e] = (k >= 0 && k < nx) ? proj(x[j * nx + k], lo, hi, project) : 0.0f;
+        xr[e] = (k >= 0 && k < nx) ? sc * proj(x[j * nx + k], lo, hi, project) : 0.0f;
     }
 }
 
 // Column-major copy (x transposed) with kPad zero entries on each side,
 // through a shared-memory tile.
 __global__ void k_pack_cols(const float *x, float *xc, int nx, int ny, long long ldc, float lo, float hi,
-                            bool project)
+                            bool project, const double *scale)
 {
     __shared__ float tile[32][33];
+    const float sc = scale ? (float)*scale : 1.0f;
     const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int iy = by + r, ix = bx + threadIdx.x;
-        tile[r][threadIdx.x] = (ix < nx && iy < ny) ? proj(x[(long long)iy * nx + ix], lo, hi, project) : 0.0f;
+        tile[r][threadIdx.x] = (ix < nx && iy < ny) ? sc * proj(x[(long long)iy * nx + ix], lo, hi, project) : 0.0f;
     }
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -182,6 +185,41 @@ __global__ void __launch_bounds__(RT) k_power_reduce(const double *pz, int nz, c
     }
 }
 
+// Per-block FP64 partial sums of v[i]^2 over fixed contiguous chunks.
+__global__ void __launch_bounds__(256) k_sumsq(const float *v, long long n, double *partials)
+{
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long b0 = (long long)blockIdx.x * per, b1 = b0 + per < n ? b0 + per : n;
+    double acc = 0.0;
+    for (long long i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        const double d = (double)v[i];
+        acc += d * d;
+    }
+    __shared__ double s[256];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = s[0];
+}
+
+// FP32 power iteration start: w = 1 (so v_1 = 1/sqrt(d) after scaling).
+__global__ void k_power_init_f(float *w, long long d, DevState *st)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d; i += (long long)gridDim.x * blockDim.x)
+        w[i] = 1.0f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->done = 0;
+        st->iters_done = 0;
+        st->status = EXACT_OK;
+        st->lam = 0.0;
+        st->lam_prev = 0.0;
+        st->inv_norm = 1.0 / sqrt((double)d);
+    }
+}
+
 unsigned grid_for(long long work, int threads)
 {
     long long b = (work + threads - 1) / threads;
@@ -193,11 +231,23 @@ unsigned grid_for(long long work, int threads)
 }  // namespace
 
 cudaError_t launch_pack(const float *x, float *xr, float *xc, int nx, int ny, long long ldr, long long ldc,
-                        float lo, float hi, bool project, cudaStream_t s)
+                        float lo, float hi, bool project, cudaStream_t s, const double *scale)
 {
-    k_pack_rows<<<grid_for((long long)ny * ldr, 256), 256, 0, s>>>(x, xr, nx, ny, ldr, lo, hi, project);
+    k_pack_rows<<<grid_for((long long)ny * ldr, 256), 256, 0, s>>>(x, xr, nx, ny, ldr, lo, hi, project, scale);
     const dim3 grid((nx + 31) / 32, (ny + 31) / 32);
-    k_pack_cols<<<grid, dim3(32, 8), 0, s>>>(x, xc, nx, ny, ldc, lo, hi, project);
+    k_pack_cols<<<grid, dim3(32, 8), 0, s>>>(x, xc, nx, ny, ldc, lo, hi, project, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(const float *v, long long n, double *partials, int nparts, cudaStream_t s)
+{
+    k_sumsq<<<nparts, 256, 0, s>>>(v, n, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_power_init_f(float *w, long long d, DevState *st, cudaStream_t s)
+{
+    k_power_init_f<<<grid_for(d, 256), 256, 0, s>>>(w, d, st);
     return cudaGetLastError();
 }
 

@@ -54,6 +54,12 @@ class _SolveInfo(ctypes.Structure):
     _fields_ = [("iters_done", ctypes.c_int), ("rel_res", ctypes.c_double), ("status", ctypes.c_int)]
 
 
+class _Job(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("y", ctypes.c_void_p), ("y_dtype", ctypes.c_int),
+                ("I0", ctypes.c_double), ("eta", ctypes.c_double), ("iters", ctypes.c_int),
+                ("opts", _SolveOpts), ("x", ctypes.c_void_p), ("info", ctypes.POINTER(_SolveInfo))]
+
+
 _lib = None
 
 # every function declared in include/exact.h: (name, restype, argtypes)
@@ -73,9 +79,14 @@ _SIGS = [
                                    ctypes.POINTER(_SolveOpts), _VP, ctypes.POINTER(_SolveInfo), _VP]),
     ("exact_norm_estimate", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int), _VP]),
+    ("exact_norm_estimate_f32", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_int), _VP]),
     ("exact_recommended_eta", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double,
                                              ctypes.POINTER(ctypes.c_double)]),
     ("exact_plan_nnz", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    ("exact_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("exact_batch_destroy", ctypes.c_int, [_VP]),
+    ("exact_batch_solve", ctypes.c_int, [_VP, ctypes.POINTER(_Job), ctypes.c_int, _VP]),
     ("exact_profile_enable", ctypes.c_int, [_VP, ctypes.c_int]),
     ("exact_profile_read", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     ("exact_status_string", _CP, [ctypes.c_int]),
@@ -267,6 +278,14 @@ class Plan:
                                                                  ctypes.byref(lam), ctypes.byref(it), _stream()))
         return lam.value, it.value
 
+    def norm_estimate_f32(self, max_iters: int = 100, rtol: float = 1e-6):
+        """Power iteration with the FP32 projector (FP64 norms); returns (lam, iterations)."""
+        lam = ctypes.c_double()
+        it = ctypes.c_int()
+        _check("exact_norm_estimate_f32", load().exact_norm_estimate_f32(
+            self._h, int(max_iters), float(rtol), ctypes.byref(lam), ctypes.byref(it), _stream()))
+        return lam.value, it.value
+
     def nnz(self) -> int:
         """Nonzero entries of A (counted on the host, cached)."""
         v = ctypes.c_longlong()
@@ -307,3 +326,72 @@ class Plan:
         _check("exact_recommended_eta", load().exact_recommended_eta(self._h, float(I0), float(normA_sq),
                                                                      ctypes.byref(eta)))
         return eta.value
+
+
+@dataclass
+class Job:
+    """One reconstruction of a batch (see exact_job)."""
+    plan: Plan
+    y: torch.Tensor
+    I0: float
+    eta: float
+    iters: int
+    x: torch.Tensor | None = None
+    lo: float = 0.0
+    hi: float = math.inf
+    tol: float = 0.0
+    check_every: int = 1
+
+
+class Batch:
+    """Persistent multi-job solver context (exact_batch_*)."""
+
+    def __init__(self, max_jobs: int = 64):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check("exact_batch_create", lib.exact_batch_create(int(max_jobs), ctypes.byref(h)))
+        self._h = h
+        self.max_jobs = max_jobs
+        self._pending = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            torch.cuda.synchronize()
+            load().exact_batch_destroy(self._h)
+            self._h = None
+            self._pending = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, jobs: list[Job], sync: bool = True):
+        """Run all jobs in one persistent launch; returns the list of SolveInfo
+        (filled once the stream passes the end of the batch) and the images."""
+        n = len(jobs)
+        arr = (_Job * n)()
+        infos = [_SolveInfo() for _ in range(n)]
+        xs = []
+        for k, jb in enumerate(jobs):
+            p = jb.plan
+            dt = p._y(jb.y)
+            x = jb.x if jb.x is not None else torch.zeros(p.shape_img, dtype=torch.float32, device=p.device)
+            p._t(x, p.shape_img, name="x")
+            xs.append(x)
+            arr[k] = _Job(p._h.value, jb.y.data_ptr(), dt, float(jb.I0), float(jb.eta), int(jb.iters),
+                          _SolveOpts(float(jb.lo), float(jb.hi), float(jb.tol), int(jb.check_every), 0),
+                          x.data_ptr(), ctypes.pointer(infos[k]))
+        _check("exact_batch_solve", load().exact_batch_solve(self._h, arr, n, _stream()))
+        if torch.cuda.is_current_stream_capturing():
+            # a captured graph writes `infos` on every replay: keep them alive
+            self._captured = getattr(self, "_captured", []) + [(arr, infos)]
+            return xs, infos
+        done = torch.cuda.Event()
+        done.record()
+        self._pending = [(e, i) for e, i in self._pending if not e.query()]
+        self._pending.append((done, (arr, infos)))
+        if sync:
+            done.synchronize()
+        return xs, infos

@@ -46,6 +46,8 @@ def test_struct_layouts_match(tmp_path):
                    'printf("%zu %zu\\n", sizeof(exact_solve_opts), offsetof(exact_solve_opts, average_tail));\n'
                    'printf("%zu %zu\\n", sizeof(exact_solve_info), offsetof(exact_solve_info, status));\n'
                    'printf("%zu %zu\\n", sizeof(exact_spectrum), sizeof(exact_windows));\n'
+                   'printf("%zu %zu %zu %zu\\n", sizeof(exact_job), offsetof(exact_job, opts), offsetof(exact_job, x),'
+                   ' offsetof(exact_job, info));\n'
                    'return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -59,6 +61,8 @@ def test_struct_layouts_match(tmp_path):
     assert i == [ctypes.sizeof(b._SolveInfo), b._SolveInfo.status.offset]
     s = [int(v) for v in out[3].split()]
     assert s == [ctypes.sizeof(b._Spectrum), ctypes.sizeof(b._Windows)]
+    jv = [int(v) for v in out[4].split()]
+    assert jv == [ctypes.sizeof(b._Job), b._Job.opts.offset, b._Job.x.offset, b._Job.info.offset]
 
 
 def test_product_path_never_imports_the_oracle():
