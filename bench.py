@@ -57,8 +57,8 @@ def parse_args(argv=None):
     p.add_argument("--batch-iters", type=int, default=None)
     p.add_argument("--no-served", action="store_true", help="skip the serving measurement")
     p.add_argument("--serve-jobs", type=int, default=32)
-    p.add_argument("--serve-load", type=float, default=0.8,
-                   help="arrival rate as a fraction of the measured sequential capacity")
+    p.add_argument("--serve-loads", default="0.8,1.5",
+                   help="arrival rates as fractions of the measured sequential capacity")
     return p.parse_args(argv)
 
 
@@ -229,9 +229,10 @@ def load_traffic(kernel: str):
     try:
         rec = json.load(open(path)).get(kernel)
         from paper_2503_19925_gb300 import _build
+        import glob
         import hashlib
         h = hashlib.sha256()
-        for src in _build.sources():
+        for src in sorted(glob.glob(os.path.join(_build.CSRC, "*"))):
             h.update(open(src, "rb").read())
         if rec and rec.get("source_sha256") == h.hexdigest():
             return rec
@@ -259,7 +260,7 @@ def make_counts(ex, torch, spec, dev, rank=0):
     return plan, y, mu, S, xs
 
 
-def run_served(ex, torch, dev, n_jobs: int, load: float, rank: int):
+def run_served(ex, torch, dev, n_jobs: int, loads, rank: int):
     """A Poisson stream of reconstruction requests (image sizes 128..512,
     90..720 views, parallel or fan beam, 1..4 windows, 16..64 energies,
     tolerance 1e-3) served (a) by the continuous-batching Server and (b) one at
@@ -290,24 +291,26 @@ def run_served(ex, torch, dev, n_jobs: int, load: float, rank: int):
     for r in reqs:
         r.arrival = 0.0
     cap = summarise(serve_sequential(reqs, realtime=False))["recon_per_s"]
-    rate = load * cap
-    rng = np.random.default_rng(55)
-    t = 0.0
-    for r in reqs:
-        t += float(rng.exponential(1.0 / rate))
-        r.arrival = t
-    server = Server(budget_bytes=configs.C5["budget_bytes"], max_slots=64, round_iters=20)
-    served = summarise(server.run(reqs, realtime=True))
-    rounds = server.rounds
-    server.close()
-    plain = summarise(serve_sequential(reqs, realtime=True))
-    return {"requests": n_jobs, "arrival_rate_per_s": rate, "load_vs_sequential_capacity": load,
-            "sequential_capacity_per_s": cap,
+    points = []
+    for load in loads:
+        rate = load * cap
+        rng = np.random.default_rng(55)
+        t = 0.0
+        for r in reqs:
+            t += float(rng.exponential(1.0 / rate))
+            r.arrival = t
+        server = Server(budget_bytes=configs.C5["budget_bytes"], max_slots=64, round_iters=20)
+        served = summarise(server.run(reqs, realtime=True))
+        served["rounds"] = server.rounds
+        server.close()
+        plain = summarise(serve_sequential(reqs, realtime=True))
+        points.append({"load_vs_sequential_capacity": load, "arrival_rate_per_s": rate, "served": served,
+                       "sequential": plain, "speedup_recon_per_s": served["recon_per_s"] / plain["recon_per_s"],
+                       "p99_latency_ratio": plain["p99_latency_s"] / served["p99_latency_s"]})
+    return {"requests": n_jobs, "sequential_capacity_per_s": cap,
             "workload": "Poisson stream; 128..512^2, 90..720 views, parallel/fan 50/50, 1..4 windows, 16..64 "
                         "energies, tol 1e-3, HBM budget 150 GB, 20 iterations per round",
-            "served": dict(served, rounds=rounds), "sequential": plain,
-            "speedup_recon_per_s": served["recon_per_s"] / plain["recon_per_s"],
-            "p99_latency_ratio": plain["p99_latency_s"] / served["p99_latency_s"]}
+            "loads": points}
 
 
 def make_job_inputs(ex, torch, spec, dev, rank=0):
@@ -547,7 +550,8 @@ def run_exact(args):
     if not args.no_batched:
         line["batched"] = run_batched(ex, torch, dev, args.batch_jobs, args.batch_iters or configs.C4["iters"], rank)
     if not args.no_served:
-        line["served"] = run_served(ex, torch, dev, args.serve_jobs, args.serve_load, rank)
+        line["served"] = run_served(ex, torch, dev, args.serve_jobs,
+                                    [float(v) for v in args.serve_loads.split(",") if v], rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_baseline_iters)
     if rank == 0:
