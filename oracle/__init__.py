@@ -102,6 +102,16 @@ def _load():
             lib.ora_h.restype = ctypes.c_double
             lib.ora_expected_counts.argtypes = [ctypes.c_long, _D, ctypes.c_int, ctypes.c_int, _D, _D,
                                                 ctypes.c_double, _D]
+            lib.ora_expected_counts_bg.argtypes = [ctypes.c_long, _D, ctypes.c_int, ctypes.c_int, _D, _D,
+                                                   ctypes.c_double, ctypes.c_int, _D, _D, _D]
+            lib.ora_residual_bg.argtypes = [ctypes.c_long, _D, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double,
+                                            ctypes.c_int, _D, _D, _D, _D]
+            lib.ora_operator_bg.argtypes = [G, _D, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double,
+                                            ctypes.c_int, _D, _D, _D, _D, _D, _D]
+            lib.ora_solve_bg.argtypes = [G, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double, ctypes.c_int, _D,
+                                         _D, _D, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_int, _D, _D, _D]
+            lib.ora_solve_bg.restype = ctypes.c_int
             lib.ora_residual.argtypes = [ctypes.c_long, _D, ctypes.c_int, ctypes.c_int, _D, _D,
                                          ctypes.c_double, _D, _D]
             lib.ora_operator.argtypes = [G, _D, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double,
@@ -118,6 +128,15 @@ def _load():
 
 def _p(a: np.ndarray):
     return a.ctypes.data_as(_D)
+
+
+def _bg(bg, n: int, K: int):
+    """Known-background arguments: bg = (mu_bg [M][K], p [M][n...]) or None."""
+    if bg is None:
+        return 0, None, None, ()
+    mu_bg = np.ascontiguousarray(bg[0], dtype=np.float64).reshape(-1, K)
+    p = np.ascontiguousarray(bg[1], dtype=np.float64).reshape(mu_bg.shape[0], n)
+    return mu_bg.shape[0], _p(mu_bg), _p(p), (mu_bg, p)
 
 
 def _f64(a) -> np.ndarray:
@@ -161,18 +180,20 @@ def h(t: float, S_w, mu) -> float:
     return _load().ora_h(float(t), len(mu), _p(S_w), _p(mu))
 
 
-def expected_counts(z, S, mu, I0: float) -> np.ndarray:
-    """Mean counts lam[w][...] = I0 h_w(z) for projections ``z`` (any shape)."""
+def expected_counts(z, S, mu, I0: float, bg=None) -> np.ndarray:
+    """Mean counts lam[w][...] = I0 h_w(z) for projections ``z`` (any shape);
+    bg = (mu_bg [M][K], p [M][...]) adds known background materials."""
     lib = _load()
     z = _f64(z)
     S, mu = _f64(S), _f64(mu)
     W, K = S.shape
     lam = np.zeros((W,) + z.shape)
-    lib.ora_expected_counts(z.size, _p(z), W, K, _p(S), _p(mu), float(I0), _p(lam))
+    M, pm, pp, keep = _bg(bg, z.size, K)
+    lib.ora_expected_counts_bg(z.size, _p(z), W, K, _p(S), _p(mu), float(I0), M, pm, pp, _p(lam))
     return lam
 
 
-def residual(z, S, mu, I0: float, y) -> np.ndarray:
+def residual(z, S, mu, I0: float, y, bg=None) -> np.ndarray:
     """r = sum_w (y[w] - I0 h_w(z)); ``y`` has shape [W] + z.shape."""
     lib = _load()
     z = _f64(z)
@@ -180,11 +201,12 @@ def residual(z, S, mu, I0: float, y) -> np.ndarray:
     W, K = S.shape
     assert y.shape == (W,) + z.shape
     r = np.zeros(z.shape)
-    lib.ora_residual(z.size, _p(z), W, K, _p(S), _p(mu), float(I0), _p(y), _p(r))
+    M, pm, pp, keep = _bg(bg, z.size, K)
+    lib.ora_residual_bg(z.size, _p(z), W, K, _p(S), _p(mu), float(I0), M, pm, pp, _p(y), _p(r))
     return r
 
 
-def operator(g: Geometry, x, S, mu, I0: float, y) -> np.ndarray:
+def operator(g: Geometry, x, S, mu, I0: float, y, bg=None) -> np.ndarray:
     """F(x) = (1/(W n)) A^T sum_w (y_w - I0 h_w(A x)); returns [ny][nx]."""
     lib = _load()
     x = _f64(x).reshape(g.ny, g.nx)
@@ -195,7 +217,9 @@ def operator(g: Geometry, x, S, mu, I0: float, y) -> np.ndarray:
     z = np.zeros(g.n_rays)
     r = np.zeros(g.n_rays)
     gc = g._c()
-    lib.ora_operator(ctypes.byref(gc), _p(x), W, K, _p(S), _p(mu), float(I0), _p(y), _p(F), _p(z), _p(r))
+    M, pm, pp, keep = _bg(bg, g.n_rays, K)
+    lib.ora_operator_bg(ctypes.byref(gc), _p(x), W, K, _p(S), _p(mu), float(I0), M, pm, pp, _p(y), _p(F), _p(z),
+                        _p(r))
     return F
 
 
@@ -209,7 +233,7 @@ class SolveResult:
 
 def solve(g: Geometry, S, mu, I0: float, y, eta: float, iters: int, x1=None,
           lo: float = 0.0, hi: float = np.inf, tol: float = 0.0, check_every: int = 1,
-          average_tail: bool = False) -> SolveResult:
+          average_tail: bool = False, bg=None) -> SolveResult:
     """Projected extragradient (Eq. (11)) on the box [lo, hi]; x1 defaults to 0."""
     lib = _load()
     S, mu, y = _f64(S), _f64(mu), _f64(y)
@@ -218,9 +242,10 @@ def solve(g: Geometry, S, mu, I0: float, y, eta: float, iters: int, x1=None,
     hist = np.zeros(max(iters, 1))
     avg = np.zeros((g.ny, g.nx)) if average_tail else None
     gc = g._c()
-    done = lib.ora_solve(ctypes.byref(gc), W, K, _p(S), _p(mu), float(I0), _p(y), float(eta), int(iters),
-                         float(lo), float(hi), float(tol), int(check_every), _p(x), _p(hist),
-                         _p(avg) if avg is not None else None)
+    M, pm, pp, keep = _bg(bg, g.n_rays, K)
+    done = lib.ora_solve_bg(ctypes.byref(gc), W, K, _p(S), _p(mu), float(I0), M, pm, pp, _p(y), float(eta),
+                            int(iters), float(lo), float(hi), float(tol), int(check_every), _p(x), _p(hist),
+                            _p(avg) if avg is not None else None)
     return SolveResult(x, done, hist[:done], avg)
 
 

@@ -169,52 +169,86 @@ void ora_adjoint(const ora_geometry *g, const double *r, double *out)
 }
 
 /* h(t) for window w: sum_k S[w][k] exp(-mu_k max(t, 0)), Eq. (7), with the
- * window's intensity folded into S (Sec. 1, Eq. (2)). */
-double ora_h(double t, int K, const double *S_w, const double *mu)
+ * window's intensity folded into S (Sec. 1, Eq. (2)), for a ray that may also
+ * cross M known materials (Appendix A.1, single-material recovery against a
+ * known background): their projections p[m * stride] attenuate energy k by
+ * exp(-mu_bg[m][k] p_m) on top of the unknown material, i.e. Eq. (1) with the
+ * known terms moved into the ray's effective intensity and spectrum. */
+double ora_h_bg(double t, int K, const double *S_w, const double *mu, int M, const double *mu_bg,
+                const double *p, long stride)
 {
     double tp = t > 0.0 ? t : 0.0;
     double s = 0.0;
-    for (int k = 0; k < K; ++k) s += S_w[k] * exp(-mu[k] * tp);
+    for (int k = 0; k < K; ++k) {
+        double e = mu[k] * tp;
+        for (int m = 0; m < M; ++m) e += mu_bg[m * K + k] * p[m * stride];
+        s += S_w[k] * exp(-e);
+    }
     return s;
 }
 
-/* Expected counts lam[w][i] = I0 h_w(z_i) (Eq. (2) with one material). */
-void ora_expected_counts(long n, const double *z, int W, int K, const double *S,
-                         const double *mu, double I0, double *lam)
+double ora_h(double t, int K, const double *S_w, const double *mu)
+{
+    return ora_h_bg(t, K, S_w, mu, 0, NULL, NULL, 0);
+}
+
+/* Expected counts lam[w][i] = I0 h_w(z_i) (Eq. (2) with one material), with
+ * an optional known background (M materials, projections p[m][i]). */
+void ora_expected_counts_bg(long n, const double *z, int W, int K, const double *S, const double *mu, double I0,
+                            int M, const double *mu_bg, const double *p, double *lam)
 {
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i)
         for (int w = 0; w < W; ++w)
-            lam[(long)w * n + i] = I0 * ora_h(z[i], K, S + (long)w * K, mu);
+            lam[(long)w * n + i] = I0 * ora_h_bg(z[i], K, S + (long)w * K, mu, M, mu_bg, p + i, n);
+}
+
+void ora_expected_counts(long n, const double *z, int W, int K, const double *S,
+                         const double *mu, double I0, double *lam)
+{
+    ora_expected_counts_bg(n, z, W, K, S, mu, I0, 0, NULL, NULL, lam);
 }
 
 /* Residual r_i = sum_w (y[w][i] - I0 h_w(z_i)): the bracket of Eq. (8), every
  * (window, ray) pair a measurement with the ray's vector a_i. */
-void ora_residual(long n, const double *z, int W, int K, const double *S,
-                  const double *mu, double I0, const double *y, double *r)
+void ora_residual_bg(long n, const double *z, int W, int K, const double *S, const double *mu, double I0, int M,
+                     const double *mu_bg, const double *p, const double *y, double *r)
 {
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) {
         double acc = 0.0;
         for (int w = 0; w < W; ++w)
-            acc += y[(long)w * n + i] - I0 * ora_h(z[i], K, S + (long)w * K, mu);
+            acc += y[(long)w * n + i] - I0 * ora_h_bg(z[i], K, S + (long)w * K, mu, M, mu_bg, p + i, n);
         r[i] = acc;
     }
 }
 
+void ora_residual(long n, const double *z, int W, int K, const double *S,
+                  const double *mu, double I0, const double *y, double *r)
+{
+    ora_residual_bg(n, z, W, K, S, mu, I0, 0, NULL, NULL, y, r);
+}
+
 /* F(x) = (1/m) sum_{w,i} (y_{w,i} - I0 h_w(<a_i,x>)) a_i with m = W * n, Eq. (8).
  * z and r are caller-provided scratch of n entries. */
-void ora_operator(const ora_geometry *g, const double *x, int W, int K, const double *S,
-                  const double *mu, double I0, const double *y, double *F,
-                  double *z, double *r)
+void ora_operator_bg(const ora_geometry *g, const double *x, int W, int K, const double *S, const double *mu,
+                     double I0, int M, const double *mu_bg, const double *p, const double *y, double *F,
+                     double *z, double *r)
 {
     long n = (long)g->n_views * g->n_bins;
     long d = (long)g->nx * g->ny;
     ora_forward(g, x, z);
-    ora_residual(n, z, W, K, S, mu, I0, y, r);
+    ora_residual_bg(n, z, W, K, S, mu, I0, M, mu_bg, p, y, r);
     ora_adjoint(g, r, F);
     double inv_m = 1.0 / ((double)W * (double)n);
-    for (long p = 0; p < d; ++p) F[p] *= inv_m;
+    for (long q = 0; q < d; ++q) F[q] *= inv_m;
+}
+
+void ora_operator(const ora_geometry *g, const double *x, int W, int K, const double *S,
+                  const double *mu, double I0, const double *y, double *F,
+                  double *z, double *r)
+{
+    ora_operator_bg(g, x, W, K, S, mu, I0, 0, NULL, NULL, y, F, z, r);
 }
 
 /* Projection onto the box [lo, hi]^d; lo = 0, hi = +inf is the projection onto
@@ -234,9 +268,9 @@ static double clampd(double v, double lo, double hi)
  * t = floor(iters/2) .. T-1, T the number of iterations run (the last
  * ceil(iters/2) iterates when the loop runs to the end; the last iterate if it
  * stopped before iters/2).  Returns T. */
-int ora_solve(const ora_geometry *g, int W, int K, const double *S, const double *mu,
-              double I0, const double *y, double eta, int iters, double lo, double hi,
-              double tol, int check_every, double *x, double *hist, double *avg)
+int ora_solve_bg(const ora_geometry *g, int W, int K, const double *S, const double *mu, double I0, int M,
+                 const double *mu_bg, const double *p, const double *y, double eta, int iters, double lo,
+                 double hi, double tol, int check_every, double *x, double *hist, double *avg)
 {
     long n = (long)g->n_views * g->n_bins;
     long d = (long)g->nx * g->ny;
@@ -250,32 +284,40 @@ int ora_solve(const ora_geometry *g, int W, int K, const double *S, const double
     int t_avg0 = iters / 2;
     long n_avg = 0;
     for (int t = 0; t < iters; ++t) {
-        ora_operator(g, x, W, K, S, mu, I0, y, F, z, r);
-        for (long p = 0; p < d; ++p) xh[p] = clampd(x[p] - eta * F[p], lo, hi);
-        ora_operator(g, xh, W, K, S, mu, I0, y, F, z, r);
-        for (long p = 0; p < d; ++p) xn[p] = clampd(x[p] - eta * F[p], lo, hi);
+        ora_operator_bg(g, x, W, K, S, mu, I0, M, mu_bg, p, y, F, z, r);
+        for (long q = 0; q < d; ++q) xh[q] = clampd(x[q] - eta * F[q], lo, hi);
+        ora_operator_bg(g, xh, W, K, S, mu, I0, M, mu_bg, p, y, F, z, r);
+        for (long q = 0; q < d; ++q) xn[q] = clampd(x[q] - eta * F[q], lo, hi);
         double num = 0.0, den = 0.0;
-        for (long p = 0; p < d; ++p) {
-            double e = xn[p] - x[p];
+        for (long q = 0; q < d; ++q) {
+            double e = xn[q] - x[q];
             num += e * e;
-            den += x[p] * x[p];
+            den += x[q] * x[q];
         }
         double rel = sqrt(num) / fmax(sqrt(den), 1e-30);
         if (hist) hist[t] = rel;
         memcpy(x, xn, sizeof(double) * d);
         if (acc && t >= t_avg0) {
-            for (long p = 0; p < d; ++p) acc[p] += x[p];
+            for (long q = 0; q < d; ++q) acc[q] += x[q];
             ++n_avg;
         }
         done = t + 1;
         if (tol > 0.0 && check_every > 0 && (t + 1) % check_every == 0 && rel <= tol) break;
     }
     if (avg) {
-        for (long p = 0; p < d; ++p) avg[p] = n_avg > 0 ? acc[p] / (double)n_avg : x[p];
+        for (long q = 0; q < d; ++q) avg[q] = n_avg > 0 ? acc[q] / (double)n_avg : x[q];
         free(acc);
     }
     free(F); free(xh); free(xn); free(z); free(r);
     return done;
+}
+
+int ora_solve(const ora_geometry *g, int W, int K, const double *S, const double *mu,
+              double I0, const double *y, double eta, int iters, double lo, double hi,
+              double tol, int check_every, double *x, double *hist, double *avg)
+{
+    return ora_solve_bg(g, W, K, S, mu, I0, 0, NULL, NULL, y, eta, iters, lo, hi, tol, check_every, x, hist,
+                        avg);
 }
 
 /* Power iteration for ||A||_op^2 = lambda_max(A^T A) (the quantity behind

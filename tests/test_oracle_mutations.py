@@ -23,12 +23,14 @@ MUTATIONS = {
     "bin_centre_off_by_half": ("double u = ((double)b - 0.5 * (double)(g->n_bins - 1))",
                                "double u = ((double)b - 0.5 * (double)(g->n_bins))"),
     "relu_dropped": ("double tp = t > 0.0 ? t : 0.0;", "double tp = t;"),
-    "residual_sign": ("acc += y[(long)w * n + i] - I0 * ora_h(z[i], K, S + (long)w * K, mu);",
-                      "acc += I0 * ora_h(z[i], K, S + (long)w * K, mu) - y[(long)w * n + i];"),
+    "residual_sign": ("acc += y[(long)w * n + i] - I0 * ora_h_bg(z[i], K, S + (long)w * K, mu, M, mu_bg, p + i, n);",
+                      "acc += I0 * ora_h_bg(z[i], K, S + (long)w * K, mu, M, mu_bg, p + i, n) - y[(long)w * n + i];"),
+    "background_sign": ("for (int m = 0; m < M; ++m) e += mu_bg[m * K + k] * p[m * stride];",
+                        "for (int m = 0; m < M; ++m) e -= mu_bg[m * K + k] * p[m * stride];"),
     "normalisation_drops_windows": ("double inv_m = 1.0 / ((double)W * (double)n);",
                                     "double inv_m = 1.0 / (double)n;"),
-    "full_step_from_half_point": ("for (long p = 0; p < d; ++p) xn[p] = clampd(x[p] - eta * F[p], lo, hi);",
-                                  "for (long p = 0; p < d; ++p) xn[p] = clampd(xh[p] - eta * F[p], lo, hi);"),
+    "full_step_from_half_point": ("for (long q = 0; q < d; ++q) xn[q] = clampd(x[q] - eta * F[q], lo, hi);",
+                                  "for (long q = 0; q < d; ++q) xn[q] = clampd(xh[q] - eta * F[q], lo, hi);"),
 }
 
 
@@ -41,7 +43,7 @@ def test_pins_catch_mutation(name, tmp_path):
     mut.write_text(src.replace(old, new))
     env = dict(os.environ, EXACT_ORACLE_SRC=str(mut), OMP_NUM_THREADS="2")
     cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-           "tests/test_oracle_projector.py", "tests/test_oracle_operator.py"]
+           "tests/test_oracle_projector.py", "tests/test_oracle_operator.py", "tests/test_oracle_background.py"]
     proc = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert proc.returncode == 1, f"mutation {name} was not caught:\n{proc.stdout[-2000:]}"
     assert " failed" in proc.stdout
