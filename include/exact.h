@@ -193,6 +193,17 @@ exact_status exact_norm_estimate_f32(exact_plan_t plan, int max_iters, double rt
  * (the Lipschitz bound of Sec. 4.2, m = n_windows * n_rays).  Host arithmetic. */
 exact_status exact_recommended_eta(exact_plan_t plan, double I0, double normA_sq, double *eta);
 
+/* Known background (Appendix A.1: recover one material while the others are
+ * known).  The rays also cross n_materials (0..4) known materials with
+ * projections p, a device array [n_materials][n_views][n_bins] FP32 (e.g.
+ * exact_forward of each known density), attenuating energy k by
+ * exp(-mu_bg[m][k] p_m) with mu_bg[m * n_energy + k] >= 0 (host, copied).  The
+ * plan keeps the pointer p (caller-owned; it must stay valid and unchanged
+ * while later operator/solve/batch calls on the plan run).  n_materials = 0
+ * removes the background.  F stays monotone and the Lipschitz bound of
+ * exact_recommended_eta still holds (the background only lowers each h_w). */
+exact_status exact_plan_set_background(exact_plan_t plan, int n_materials, const double *mu_bg, const float *p);
+
 /* ---- Batched solves (many reconstructions in one persistent launch) ---- */
 
 typedef struct exact_batch *exact_batch_t;

@@ -380,6 +380,7 @@ LinkCoef make_coef(const Plan &P, double I0)
     for (int k = 0; k < P.K; ++k) {
         c.mu2[k] = P.mu_log2e[k];
         c.c[k] = (float)(I0 * (double)P.C[k]);
+        for (int m = 0; m < P.bg_M; ++m) c.mub[m][k] = P.bg_mu2[m][k];
     }
     return c;
 }
@@ -732,6 +733,8 @@ exact_status exact_operator(exact_plan_t plan, const float *x, const void *y, ex
     f.Y = P.Y;
     f.r = P.r;
     f.K = P.K;
+    f.M = P.bg_M;
+    f.bg = P.bg_p;
     EXACT_TRY(launch_forward(f, true, &coef, P.maps_r[0], P.maps_c[0], s));
     AdjArgs a;
     memset(&a, 0, sizeof(a));
@@ -787,6 +790,8 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     f.Y = P.Y;
     f.r = P.r;
     f.K = P.K;
+    f.M = P.bg_M;
+    f.bg = P.bg_p;
     f.state = P.state;
     AdjArgs a;
     memset(&a, 0, sizeof(a));
@@ -948,6 +953,25 @@ exact_status exact_recommended_eta(exact_plan_t plan, double I0, double normA_sq
     const double m = (double)P->W * (double)P->n;
     const double L = I0 * normA_sq / m * P->Csum_mu;
     *eta = 1.0 / (4.0 * L);
+    return EXACT_OK;
+}
+
+exact_status exact_plan_set_background(exact_plan_t plan, int n_materials, const double *mu_bg, const float *p)
+{
+    if (!plan || n_materials < 0 || n_materials > kMaxBg) return EXACT_ERR_INVALID_ARG;
+    Plan *P = reinterpret_cast<Plan *>(plan);
+    if (n_materials == 0) {
+        P->bg_M = 0;
+        P->bg_p = nullptr;
+        return EXACT_OK;
+    }
+    if (!mu_bg || !p) return EXACT_ERR_INVALID_ARG;
+    for (int q = 0; q < n_materials * P->K; ++q)
+        if (!isfin(mu_bg[q]) || mu_bg[q] < 0.0) return EXACT_ERR_INVALID_ARG;
+    for (int m = 0; m < n_materials; ++m)
+        for (int k = 0; k < P->K; ++k) P->bg_mu2[m][k] = (float)(mu_bg[m * P->K + k] * 1.4426950408889634);
+    P->bg_M = n_materials;
+    P->bg_p = p;
     return EXACT_OK;
 }
 
@@ -1175,6 +1199,8 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
         J.f.Y = P.Y;
         J.f.r = P.r;
         J.f.K = P.K;
+        J.f.M = P.bg_M;
+        J.f.bg = P.bg_p;
         J.a.rays = P.rays_f;
         J.a.views = P.views;
         J.a.n_views = P.g.n_views;

@@ -22,6 +22,7 @@ constexpr int kPad = 2;
 constexpr float kFloorMagic = 12582912.0f;  // 1.5 * 2^23
 constexpr int kFloorBias = 0x4B400000;      // bit pattern of kFloorMagic
 constexpr int kMaxK = EXACT_MAX_ENERGY;
+constexpr int kMaxBg = 4;  // known background materials per plan
 
 // One ray of the Joseph projector, FP32 form.  The cross-axis pixel-index
 // coordinate of the crossing at driving index j is t(j) = alpha + beta j
@@ -118,6 +119,9 @@ struct Plan {
     int n_units = 0;
     // tensor maps of the padded copies: maps_r[q] over xr[q], maps_c[q] over xc[q]
     CUtensorMap maps_r[2], maps_c[2];
+    int bg_M = 0;                    // known background (exact_plan_set_background)
+    const float *bg_p = nullptr;     // caller-owned [bg_M][n]
+    float bg_mu2[kMaxBg][kMaxK];     // mu_bg log2(e)
     std::vector<void *> captured_infos;  // solve-info payloads owned by captured graphs
     // kernel timing (profiling aid): event pairs recorded around sampled launches
     int prof_every = 0;
@@ -154,13 +158,16 @@ struct FwdArgs {
     const float *Y;       // collapsed counts (link == true)
     float *r;             // residual output times delta (link == true)
     int K;
+    int M;                  // known background materials (0: none)
+    const float *bg;        // [M][n] their projections
     const DevState *state;  // may be null: if set and state->done, return
 };
 
 // Link coefficients passed by value (kernel parameter space).
 struct LinkCoef {
-    float mu2[kMaxK];  // mu_k log2(e)
-    float c[kMaxK];    // I0 sum_w S[w][k]
+    float mu2[kMaxK];          // mu_k log2(e)
+    float c[kMaxK];            // I0 sum_w S[w][k]
+    float mub[kMaxBg][kMaxK];  // known-background attenuation mu_bg[m][k] log2(e)
 };
 
 enum AdjMode { ADJ_PLAIN = 0, ADJ_EG = 1, ADJ_EG_FINAL = 2 };

@@ -173,7 +173,20 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
     }
     const float zp = fmaxf(z, 0.0f);
     float lam = 0.0f;
-    for (int k = 0; k < a.K; ++k) lam = fmaf(coef->c[k], exp2f(-coef->mu2[k] * zp), lam);
+    if (a.M == 0) {
+        for (int k = 0; k < a.K; ++k) lam = fmaf(coef->c[k], exp2f(-coef->mu2[k] * zp), lam);
+    } else {
+        // known background (Appendix A.1): extra attenuation sum_m mu_bg[m][k] p_m
+        float pm[kMaxBg];
+#pragma unroll
+        for (int m = 0; m < kMaxBg; ++m) pm[m] = m < a.M ? a.bg[(long long)m * a.n + i] : 0.0f;
+        for (int k = 0; k < a.K; ++k) {
+            float e = coef->mu2[k] * zp;
+#pragma unroll
+            for (int m = 0; m < kMaxBg; ++m) e = fmaf(coef->mub[m][k], pm[m], e);
+            lam = fmaf(coef->c[k], exp2f(-e), lam);
+        }
+    }
     a.r[i] = delta * (a.Y[i] - lam);
     return true;
 }

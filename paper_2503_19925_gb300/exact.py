@@ -84,6 +84,7 @@ _SIGS = [
     ("exact_recommended_eta", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double,
                                              ctypes.POINTER(ctypes.c_double)]),
     ("exact_plan_nnz", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    ("exact_plan_set_background", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP]),
     ("exact_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_VP)]),
     ("exact_batch_destroy", ctypes.c_int, [_VP]),
     ("exact_batch_solve", ctypes.c_int, [_VP, ctypes.POINTER(_Job), ctypes.c_int, _VP]),
@@ -285,6 +286,20 @@ class Plan:
         _check("exact_norm_estimate_f32", load().exact_norm_estimate_f32(
             self._h, int(max_iters), float(rtol), ctypes.byref(lam), ctypes.byref(it), _stream()))
         return lam.value, it.value
+
+    def set_background(self, mu_bg=None, p: torch.Tensor | None = None):
+        """Known background materials (Appendix A.1): mu_bg [M][K] attenuations,
+        p [M][n_views][n_bins] device FP32 projections (kept referenced)."""
+        if p is None:
+            _check("exact_plan_set_background", load().exact_plan_set_background(self._h, 0, None, None))
+            self._bg = None
+            return
+        rows = [[float(v) for v in r] for r in mu_bg]
+        M = len(rows)
+        self._t(p, (M,) + self.shape_sino, name="p")
+        arr = (ctypes.c_double * (M * self.K))(*[v for r in rows for v in r])
+        _check("exact_plan_set_background", load().exact_plan_set_background(self._h, M, arr, _ptr(p)))
+        self._bg = p
 
     def nnz(self) -> int:
         """Nonzero entries of A (counted on the host, cached)."""

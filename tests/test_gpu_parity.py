@@ -260,3 +260,34 @@ def test_c3_solve_first_iterations_and_norm(c3):
     x, info = plan.solve(_gpu(p["y"], torch.bfloat16), p["I0"], eta, 3)
     refx = oracle.solve(p["g_or"], p["S"], p["mu"], p["I0"], p["y"], eta, 3)
     assert rel_l2(x.double().cpu().numpy(), refx.x) <= 1e-4
+
+
+@pytest.mark.parametrize("gi", [0, 2])
+def test_known_background_operator_and_solve(gi):
+    """Appendix A.1: known materials enter through their projections."""
+    geom = GEOMS[gi]
+    p = problem(geom, K=16, W=2, I0=1e4, seed=60 + gi)
+    e = synth.energy_grid(16)
+    mu_bg = np.stack([synth.power_law_mu(e, 0.03) + 0.002, synth.power_law_mu(e, 0.08)])
+    g_or = p["g_or"]
+    xb = [synth.random_image(geom["nx"], geom["ny"], seed=5 + m, hi=0.3) for m in range(2)]
+    pb = np.stack([oracle.forward(g_or, x) for x in xb])
+    lam = oracle.expected_counts(oracle.forward(g_or, p["xs"]), p["S"], p["mu"], p["I0"], bg=(mu_bg, pb))
+    y = synth.poisson_counts(lam, 3)
+    plan = _plan(geom, p["S"], p["mu"])
+    pg = _gpu(pb)
+    plan.set_background(mu_bg, pg)
+    x = 0.5 * p["xs"]
+    F = plan.operator(_gpu(x), _gpu(y), p["I0"]).double().cpu().numpy()
+    ref = oracle.operator(g_or, x, p["S"], p["mu"], p["I0"], y, bg=(mu_bg, pb))
+    assert rel_l2(F, ref) <= 1e-5
+    eta = _eta(p)
+    xg, info = plan.solve(_gpu(y), p["I0"], eta, 30)
+    xr = oracle.solve(g_or, p["S"], p["mu"], p["I0"], y, eta, 30, bg=(mu_bg, pb))
+    assert rel_l2(xg.double().cpu().numpy(), xr.x) <= 1e-3
+    # and the batch path uses the same background
+    xs, infos = ex.Batch(2).solve([ex.Job(plan=plan, y=_gpu(y), I0=p["I0"], eta=eta, iters=30)])
+    assert rel_l2(xs[0].double().cpu().numpy(), xr.x) <= 1e-3
+    plan.set_background()
+    F0 = plan.operator(_gpu(x), _gpu(y), p["I0"]).double().cpu().numpy()
+    assert rel_l2(F0, oracle.operator(g_or, x, p["S"], p["mu"], p["I0"], y)) <= 1e-5
