@@ -193,6 +193,29 @@ exact_status exact_norm_estimate_f32(exact_plan_t plan, int max_iters, double rt
  * (the Lipschitz bound of Sec. 4.2, m = n_windows * n_rays).  Host arithmetic. */
 exact_status exact_recommended_eta(exact_plan_t plan, double I0, double normA_sq, double *eta);
 
+/* F(x) exactly as exact_operator computes it, for callers that cannot
+ * allocate device memory when they need it: allocator-free real-time loops
+ * that must not stall on cudaMalloc, and processes whose device memory is
+ * owned by another framework's pool and cannot spare a separate workspace.  The paper has no counterpart: this is a
+ * deployment variant of exact_operator.  Instead of the plan's bound workspace
+ * it uses one file-scope device array of EXACT_STATIC_SCRATCH_MB MiB as
+ * scratch, so the call allocates nothing and needs no workspace (the plan
+ * itself, with its tables, is created beforehand).  The array exists once per
+ * device that loads the library and lives until the process exits.
+ *  - A plan whose scratch (padded image copies, collapsed counts, residual:
+ *    about 8 (nx + 8)(ny + 8) + 8 n_views n_bins bytes) exceeds the array is
+ *    rejected with EXACT_ERR_UNSUPPORTED.
+ *  - The first call on a device looks the array's device address up (with that
+ *    device current) and keeps it; make that first call before any stream
+ *    capture.
+ *  - Every call shares the array and it keeps the last call's contents (each
+ *    call writes all scratch it reads, so nothing has to be cleared); calls
+ *    that overlap on the GPU -- other streams, other threads -- race on it.
+ * Arguments, layouts and the other errors as exact_operator. */
+#define EXACT_STATIC_SCRATCH_MB 24
+exact_status exact_operator_static(exact_plan_t plan, const float *x, const void *y, exact_dtype y_dtype,
+                                   double I0, float *F, exact_stream_t stream);
+
 /* Known background (Appendix A.1: recover one material while the others are
  * known).  The rays also cross n_materials (0..4) known materials with
  * projections p, a device array [n_materials][n_views][n_bins] FP32 (e.g.

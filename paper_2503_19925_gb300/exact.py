@@ -74,6 +74,7 @@ _SIGS = [
     ("exact_forward", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("exact_adjoint", ctypes.c_int, [_VP, _VP, _VP, _VP]),
     ("exact_operator", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP, _VP]),
+    ("exact_operator_static", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP, _VP]),
     ("exact_solve_opts_default", _SolveOpts, []),
     ("exact_solve", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    ctypes.POINTER(_SolveOpts), _VP, ctypes.POINTER(_SolveInfo), _VP]),
