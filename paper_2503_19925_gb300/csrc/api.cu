@@ -78,7 +78,40 @@ void ray_line(const exact_geometry &g, int v, int b, double &px, double &py, dou
 struct RayHost {
     int axis, jlo, jhi;
     double alpha, beta, delta;
+    double ka, kb, sg;  // walk coefficients (RayW)
 };
+
+// Walk coefficients of ray (v, b) on driving axis `axis`: d alpha/d b,
+// d beta/d b and the Moebius parameter sg (see RayW).  Fan beam, x driving:
+// the ray direction from the source is E = (-R_d c - s u, -R_d s + c u);
+// beta = E_y / E_x, so d beta/d u = -R_d / E_x^2 and one bin further on
+// beta changes by (d beta/d b) e / (1 - s pitch e / E_x); alpha is affine in
+// beta.  y driving swaps the roles.  Parallel beam: alpha is affine in u and
+// beta constant.
+void walk_coefs(const exact_geometry &g, int v, int b, int axis, double &ka, double &kb, double &sg)
+{
+    const double th = g.angle0 + (double)v * g.angle_range / (double)g.n_views;
+    const double c = cos(th), s = sin(th), p = g.pixel, h = g.bin_pitch;
+    if (g.beam == 0) {
+        ka = axis == 0 ? h / (c * p) : -h / (s * p);
+        kb = 0.0;
+        sg = 0.0;
+        return;
+    }
+    const double u = ((double)b - 0.5 * (double)(g.n_bins - 1)) * h + g.det_offset;
+    const double Rs = g.src_to_center, Rd = g.src_to_det;
+    if (axis == 0) {
+        const double ex = -Rd * c - s * u, x0 = -0.5 * (double)(g.nx - 1) * p;
+        kb = -Rd * h / (ex * ex);
+        sg = -s * h / ex;
+        ka = (x0 - Rs * c) / p * kb;
+    } else {
+        const double ey = -Rd * s + c * u, y0 = -0.5 * (double)(g.ny - 1) * p;
+        kb = Rd * h / (ey * ey);
+        sg = c * h / ey;
+        ka = (y0 - Rs * s) / p * kb;
+    }
+}
 
 RayHost make_ray(const exact_geometry &g, int v, int b)
 {
@@ -103,6 +136,7 @@ RayHost make_ray(const exact_geometry &g, int v, int b)
         nd = g.ny;
         nc = g.nx;
     }
+    walk_coefs(g, v, b, r.axis, r.ka, r.kb, r.sg);
     // driving indices whose crossing lies in (-1.5, nc + 0.5): a superset of
     // the samples that touch the image, half a pixel of margin for FP32 t
     const double tlo = -1.5, thi = (double)nc + 0.5;
@@ -515,6 +549,7 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
 
     const exact_geometry &g = *geometry;
     std::vector<RayF> rf((size_t)P->n);
+    std::vector<RayW> rw((size_t)P->n);
     std::vector<int> rbits((size_t)P->n);
     std::vector<float> rdelta((size_t)P->n);
     std::vector<RayD> rd((size_t)P->n);
@@ -533,6 +568,10 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
             rf[i].a = (float)(h.alpha - A);
             rf[i].bh = bh;
             rf[i].bl = (float)(h.beta - (double)bh);
+            rw[i].ka = (float)h.ka;
+            rw[i].kb = (float)h.kb;
+            rw[i].sg = (float)h.sg;
+            rw[i].pad = 0.0f;
             rbits[i] = bits;
             rdelta[i] = (float)h.delta;
             rd[i].alpha = h.alpha;
@@ -569,6 +608,8 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
     if (kst.empty()) kst.push_back(0);
     P->n_units = (int)units.size();
     cudaError_t e = cudaMalloc(&P->rays_f, sizeof(RayF) * rf.size());
+    if (e == cudaSuccess) e = cudaMalloc(&P->rays_w, sizeof(RayW) * rw.size());
+    if (e == cudaSuccess) e = cudaMemcpy(P->rays_w, rw.data(), sizeof(RayW) * rw.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&P->units, sizeof(FwdUnit) * units.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->kstart, sizeof(int) * kst.size());
     if (e == cudaSuccess) e = cudaMemcpy(P->units, units.data(), sizeof(FwdUnit) * units.size(), cudaMemcpyHostToDevice);
@@ -601,6 +642,7 @@ exact_status exact_plan_destroy(exact_plan_t plan)
     cudaGetDevice(&prev);
     if (P->device >= 0 && prev != P->device) cudaSetDevice(P->device);
     if (P->rays_f) cudaFree(P->rays_f);
+    if (P->rays_w) cudaFree(P->rays_w);
     if (P->units) cudaFree(P->units);
     if (P->kstart) cudaFree(P->kstart);
     if (P->ray_bits) cudaFree(P->ray_bits);
@@ -694,6 +736,7 @@ exact_status exact_adjoint(exact_plan_t plan, const float *r, float *g, exact_st
     AdjArgs a;
     memset(&a, 0, sizeof(a));
     a.rays = P.rays_f;
+    a.walk = P.rays_w;
     a.views = P.views;
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
@@ -739,6 +782,7 @@ exact_status exact_operator(exact_plan_t plan, const float *x, const void *y, ex
     AdjArgs a;
     memset(&a, 0, sizeof(a));
     a.rays = P.rays_f;
+    a.walk = P.rays_w;
     a.views = P.views;
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
@@ -796,6 +840,7 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     AdjArgs a;
     memset(&a, 0, sizeof(a));
     a.rays = P.rays_f;
+    a.walk = P.rays_w;
     a.views = P.views;
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
@@ -912,6 +957,7 @@ exact_status exact_norm_estimate_f32(exact_plan_t plan, int max_iters, double rt
     AdjArgs a;
     memset(&a, 0, sizeof(a));
     a.rays = P.rays_f;
+    a.walk = P.rays_w;
     a.views = P.views;
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
@@ -1202,6 +1248,7 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
         J.f.M = P.bg_M;
         J.f.bg = P.bg_p;
         J.a.rays = P.rays_f;
+        J.a.walk = P.rays_w;
         J.a.views = P.views;
         J.a.n_views = P.g.n_views;
         J.a.n_bins = P.g.n_bins;
@@ -1217,8 +1264,8 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
         J.a.partials = P.partials;
         J.a.state = P.state;
         J.n_units = P.n_units;
-        J.tiles_x = (P.g.nx + 31) / 32;
-        J.tiles_y = (P.g.ny + 7) / 8;
+        J.tiles_x = (P.g.nx + kTW - 1) / kTW;
+        J.tiles_y = (P.g.ny + kTH - 1) / kTH;
         J.fan = P.g.beam == 1;
         J.iters = Jb.iters;
         J.check_every = Jb.opts.check_every;

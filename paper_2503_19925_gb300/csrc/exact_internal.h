@@ -35,6 +35,17 @@ struct __align__(16) RayF {
     float A, a, bh, bl;
 };
 
+// Walk coefficients of one ray, for the adjoint's strip walk.  Along the rays
+// of one view that share a driving axis, the crossing of driving line j is a
+// Moebius function of the bin index: for bins b + e (e a small integer),
+//   t_{b+e}(j) = t_b(j) + kappa e / (1 + sg e),   kappa = ka + kb j,
+// with ka = d alpha / d b, kb = d beta / d b at bin b and sg the relative change
+// of the ray's driving-axis direction component per bin (0 for parallel beams,
+// where kb = 0 too).  Computed in FP64 on the host.
+struct __align__(16) RayW {
+    float ka, kb, sg, pad;
+};
+
 // Per-ray driving range and axis: bits 0-14 first driving index j_lo,
 // 15-29 last j_hi, 30 driving axis (0: x drives, the image is read through the
 // column-major copy; 1: y drives, row-major copy).  An empty range has
@@ -68,6 +79,10 @@ struct __align__(16) ViewRec {
 constexpr int kFR = 128;   // rays per unit (threads per CTA)
 constexpr int kFC = 16;    // driving lines per staged chunk
 constexpr int kFHB = 256;  // staged cross-axis rows per chunk (tensor-map box height)
+// Adjoint tile (pixels): one CTA gathers A^T r over kTW x kTH pixels.
+constexpr int kTW = 16;
+constexpr int kTH = 16;
+
 struct __align__(16) FwdUnit {
     int ray0, count, axis, jc0;
     int nchunks, koff, pad0, pad1;
@@ -94,6 +109,7 @@ struct Plan {
     float mu_log2e[kMaxK];         // mu_k * log2(e), FP32
     float C[kMaxK];                // sum_w S[w][k], FP32 (multiplied by I0 per call)
     RayF *rays_f = nullptr;        // [n]
+    RayW *rays_w = nullptr;        // [n] walk coefficients (adjoint)
     int *ray_bits = nullptr;       // [n] driving range and axis
     float *ray_delta = nullptr;    // [n] step length delta
     RayD *rays_d = nullptr;        // [n]
@@ -174,6 +190,7 @@ enum AdjMode { ADJ_PLAIN = 0, ADJ_EG = 1, ADJ_EG_FINAL = 2 };
 
 struct AdjArgs {
     const RayF *rays;
+    const RayW *walk;
     const ViewRec *views;
     int n_views, n_bins, nx, ny;
     const float *r;        // [n] residual; already times delta unless `delta` is set

@@ -109,8 +109,12 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
     for (int c = 0; c < u.nchunks; ++c) {
         const int b = c & 1;
         if (t == 0) {
-            const bool ok = mbar_wait(&bar[b], ph[b] & 1u);
-            if (ok) ph[b] += 1;
+            // (ph indexed with constants so that it stays in registers)
+            const bool ok = mbar_wait(&bar[b], (b ? ph[1] : ph[0]) & 1u);
+            if (ok) {
+                if (b) ph[1] += 1;
+                else ph[0] += 1;
+            }
             *s_ok = ok ? 1 : 0;
             if (ok && c + 1 < u.nchunks) {
                 // the other buffer was last read before the barrier that ended
@@ -124,7 +128,7 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
             // the copy of chunk c never completed: report, wait (bounded) for
             // it once more so no copy lands after the buffers are released
             if (t == 0) {
-                mbar_wait(&bar[b], ph[b] & 1u);
+                mbar_wait(&bar[b], (b ? ph[1] : ph[0]) & 1u);
                 if (a.err) {
                     a.err->status = EXACT_ERR_TIMEOUT;
                     a.err->done = 1;
@@ -193,15 +197,17 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
 
 // ------------------------------------------------------------------ adjoint
 
-constexpr int kTW = 32;         // tile width (pixels) = lanes of a warp
-constexpr int kTH = 8;          // tile height = strip length of both walks
+// Tile kTW x kTH (exact_internal.h).  Each half-warp walks its own views; lane
+// l % 16 of a half owns one tile column (x-driven rays) and one tile row
+// (y-driven rays), so both strips are kTH = kTW pixels long.
+static_assert(kTW == 16 && kTH == 16, "a half-warp covers one tile side");
 constexpr int kRows = kTH + 2;  // accumulator rows: strip offsets -1 .. kTH
-static_assert(kTW % kTH == 0, "y-driven lanes split a tile row into whole segments");
+constexpr int kAccLd = 32;      // accumulator row stride: word (row, lane)
 constexpr float kBinEps = 0.01f;
 
 template <int G>
 struct AdjSmem {
-    float acc[G][2][kRows * kTW];  // per warp: x-driven then y-driven accumulators
+    float acc[G][2][kRows * kAccLd];  // per warp: x-driven then y-driven accumulators
     float stage[kTH][kTW + 1];
     float tile[kTH][kTW + 1];
     double red0[G], red1[G];
@@ -224,61 +230,74 @@ __device__ __forceinline__ void seg_range(float num1, float den1, float num2, fl
 }
 
 // Walk rays b0..b1 of one view at driving index jf; deposit into acc rows
-// k + 1 and k + 2 (strip offset k = floor(t - kbase) in [-1, kTH - 1]).
-template <bool DELTA, bool COHERENT>
-__device__ __forceinline__ void strip_walk(const RayF *__restrict__ vrays, const float *__restrict__ vres,
-                                           const float *__restrict__ vdelta, int b0, int b1, float jf, float kbase,
-                                           float *__restrict__ acc, int lane)
+// k + 1 and k + 2 (strip offset k = floor(t - kbase) in [-1, kTH - 1]).  The
+// crossing of the middle ray bc is computed from its split record; the others
+// follow from the walk coefficients (RayW) as
+//   t_{bc+e} = t_bc + kappa e - kappa sg e^2 / (1 + sg e),
+// so a step reads only its residual.  |e| <= 1/2 of the walk keeps the
+// FP32 error of t near 1e-6 pixel.
+template <bool FAN, bool DELTA, bool COHERENT>
+__device__ __forceinline__ void strip_walk(const RayF *__restrict__ vrays, const RayW *__restrict__ vwalk,
+                                           const float *__restrict__ vres, const float *__restrict__ vdelta,
+                                           int b0, int b1, float jf, float kbase, float *__restrict__ acc, int lane)
 {
-    for (int b = b0; b <= b1; ++b) {
-        const float4 q = __ldg(reinterpret_cast<const float4 *>(vrays + b));
-        const RayF rec = {q.x, q.y, q.z, q.w};
+    if (b0 > b1) return;
+    const int bc = (b0 + b1) >> 1;
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(vrays + bc));
+    const float4 w = __ldg(reinterpret_cast<const float4 *>(vwalk + bc));
+    const float p = q.z * jf;
+    const float pe = fmaf(q.z, jf, -p);
+    const float tc = ((q.x - kbase) + p) + (q.y + fmaf(q.w, jf, pe));
+    const float kap = fmaf(w.y, jf, w.x);
+    const float ks = kap * w.z;
+    float e = (float)(b0 - bc);
+    for (int b = b0; b <= b1; ++b, e += 1.0f) {
         float rv = ld_dyn<COHERENT>(vres + b);
         if (DELTA) rv *= __ldg(vdelta + b);
-        const float p = rec.bh * jf;
-        const float e = fmaf(rec.bh, jf, -p);
-        const float u = ((rec.A - kbase) + p) + (rec.a + fmaf(rec.bl, jf, e));
+        float u = fmaf(kap, e, tc);
+        if (FAN) u = fmaf(-(ks * e) * e, __fdividef(1.0f, fmaf(w.z, e, 1.0f)), u);
         // floor(u) without the conversion pipe (|u| < 2^22)
         const float r = __fadd_rd(u, kFloorMagic);
         const float f = u - (r - kFloorMagic);
         const int k = __float_as_int(r) - kFloorBias;
-        if (k >= -1 && k < kTH) {
+        if ((unsigned)(k + 1) < (unsigned)(kTH + 1)) {
             const float w1 = f * rv;
-            acc[(k + 1) * kTW + lane] += rv - w1;
-            acc[(k + 2) * kTW + lane] += w1;
+            acc[(k + 1) * kAccLd + lane] += rv - w1;
+            acc[(k + 2) * kAccLd + lane] += w1;
         }
     }
 }
 
 // A^T r over tile (bx, by) with the epilogue of MODE (see k_adjoint.cu).
-// blk is the tile's index for the partial norms.  Uses G warps.
+// blk is the tile's index for the partial norms.  Uses G warps (2G half-warps,
+// half-warp q takes views q, q + 2G, ...).
 template <int MODE, bool FAN, bool DELTA, int G, bool COHERENT>
 __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, long long blk, AdjSmem<G> &sm)
 {
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, l = lane & 15;
     float *accx = sm.acc[g][0];
     float *accy = sm.acc[g][1];
     for (int r = 0; r < kRows; ++r) {
-        accx[r * kTW + lane] = 0.0f;
-        accy[r * kTW + lane] = 0.0f;
+        accx[r * kAccLd + lane] = 0.0f;
+        accy[r * kAccLd + lane] = 0.0f;
     }
     const int tx0 = bx * kTW, ty0 = by * kTH;
     // x-driven strip of this lane: column cx, rows ty0 .. ty0 + kTH - 1
-    const int cx = tx0 + lane;
+    const int cx = tx0 + l;
     const bool xok = cx < a.nx;
     // strip end points, kept within one pixel of the image so that their
     // fan-beam projections stay well defined (the source is outside the image)
     const float fcx = (float)cx, fy_lo = (float)(ty0 - 1), fy_hi = (float)min(ty0 + kTH, a.ny);
-    // y-driven strip of this lane: row ry, columns cy0 .. cy0 + kTH - 1
-    const int ry = ty0 + (lane % kTH);
-    const int cy0 = tx0 + kTH * (lane / kTH);
-    const bool yok = ry < a.ny && cy0 < a.nx;
-    const float fry = (float)ry, fx_lo = (float)(cy0 - 1), fx_hi = (float)min(cy0 + kTH, a.nx);
+    // y-driven strip of this lane: row ry, columns tx0 .. tx0 + kTW - 1
+    const int ry = ty0 + l;
+    const bool yok = ry < a.ny;
+    const float fry = (float)ry, fx_lo = (float)(tx0 - 1), fx_hi = (float)min(tx0 + kTW, a.nx);
 
-    for (int v = g; v < a.n_views; v += G) {
+    for (int v = 2 * g + (lane >> 4); v < a.n_views; v += 2 * G) {
         const ViewRec vr = a.views[v];
         const long long vb = (long long)v * a.n_bins;
         const RayF *vrays = a.rays + vb;
+        const RayW *vwalk = a.walk + vb;
         const float *vres = a.r + vb;
         const float *vdel = DELTA ? a.delta + vb : nullptr;
         if (vr.xb1 > vr.xb0 && xok) {
@@ -286,32 +305,34 @@ __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, l
             int b0, b1;
             seg_range<FAN>(fmaf(vr.n2, fy_lo, nb), fmaf(vr.d2, fy_lo, db), fmaf(vr.n2, fy_hi, nb),
                            fmaf(vr.d2, fy_hi, db), vr.c, vr.xb0, vr.xb1, b0, b1);
-            strip_walk<DELTA, COHERENT>(vrays, vres, vdel, b0, b1, fcx, (float)ty0, accx, lane);
+            strip_walk<FAN, DELTA, COHERENT>(vrays, vwalk, vres, vdel, b0, b1, fcx, (float)ty0, accx, lane);
         }
         if (vr.yb1 > vr.yb0 && yok) {
             const float nb = fmaf(vr.n2, fry, vr.n0), db = fmaf(vr.d2, fry, vr.d0);
             int b0, b1;
             seg_range<FAN>(fmaf(vr.n1, fx_lo, nb), fmaf(vr.d1, fx_lo, db), fmaf(vr.n1, fx_hi, nb),
                            fmaf(vr.d1, fx_hi, db), vr.c, vr.yb0, vr.yb1, b0, b1);
-            strip_walk<DELTA, COHERENT>(vrays, vres, vdel, b0, b1, fry, (float)cy0, accy, lane);
+            strip_walk<FAN, DELTA, COHERENT>(vrays, vwalk, vres, vdel, b0, b1, fry, (float)tx0, accy, lane);
         }
     }
     __syncthreads();
 
-    // fixed-order reduction over the warps: the y-driven parts first, staged
-    // transposed (row stride kTW + 1), then the x-driven parts
+    // fixed-order reduction over the warps and their halves: the y-driven
+    // parts first, staged transposed (row stride kTW + 1), then the x-driven
+    // parts
     for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
-        const int l = t % kTW, k = t / kTW;  // accy column l, strip offset k
+        const int rl = t % kTH, k = t / kTH;  // tile row rl (y lane), column offset k
         float s = 0.0f;
-        for (int q = 0; q < G; ++q) s += sm.acc[q][1][(k + 1) * kTW + l];
-        sm.stage[l % kTH][kTH * (l / kTH) + k] = s;
+        for (int q = 0; q < G; ++q) s += sm.acc[q][1][(k + 1) * kAccLd + rl] + sm.acc[q][1][(k + 1) * kAccLd + 16 + rl];
+        sm.stage[rl][k] = s;
     }
     __syncthreads();
     double s0 = 0.0, s1 = 0.0;
     for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
         const int px = t % kTW, py = t / kTW;
         float gsum = sm.stage[py][px];
-        for (int q = 0; q < G; ++q) gsum += sm.acc[q][0][(py + 1) * kTW + px];
+        for (int q = 0; q < G; ++q)
+            gsum += sm.acc[q][0][(py + 1) * kAccLd + px] + sm.acc[q][0][(py + 1) * kAccLd + 16 + px];
         const int kx = tx0 + px, ky = ty0 + py;
         const bool inside = kx < a.nx && ky < a.ny;
         if (MODE == ADJ_PLAIN) {

@@ -4,7 +4,7 @@
 //
 // Work items.  A round of job j is one extragradient iteration (Eq. (11)) in
 // five phases: forward+link on x_t (one item per forward work unit), adjoint
-// half step (one item per 32x8 tile), forward+link on x_{t+1/2}, adjoint full
+// half step (one item per 16x16 tile), forward+link on x_{t+1/2}, adjoint full
 // step, and the FP64 stopping reduction (one item).  Items are handed out in a
 // fixed global order -- round-major, then phase, then job, then item -- by an
 // atomic counter; every CTA loops: take the next item, wait until all items

@@ -82,7 +82,7 @@ def footprint_bytes(geometry: Geometry, W: int, y_itemsize: int) -> int:
     n = geometry.n_views * geometry.n_bins
     d = geometry.nx * geometry.ny
     ldr, ldc = geometry.nx + 8, geometry.ny + 8
-    tables = n * (16 + 4 + 4 + 32) + geometry.n_views * 48 + (n // 16 + 1) * 32 * 8
+    tables = n * (16 + 16 + 4 + 4 + 32) + geometry.n_views * 48 + (n // 16 + 1) * 32 * 8
     ws = 4 * 2 * (geometry.ny * ldr + geometry.nx * ldc) + 8 * n + 8 * (geometry.ny * ldr + geometry.nx * ldc) \
         + 8 * n + 8 * d + 4 * d + (1 << 20)
     return tables + ws + W * n * y_itemsize + 4 * d
