@@ -75,14 +75,16 @@ struct FwdSmem {
 // ------------------------------------------------------------------ forward
 
 // Joseph forward walk of work unit `ui` (see k_forward.cu for the design).
-// Thread 0 owns the two mbarriers; ph[b] counts the completed phases of
-// barrier b across calls (both start at 0 after mbar_init).  Returns false
-// (uniformly) if a staging copy timed out; the caller must then stop using the
-// shared buffers.
+// Thread 0 issues the copies; every thread waits on the two mbarriers and
+// keeps ph[b], the completed phases of barrier b across calls (both start at 0
+// after mbar_init).  One CTA barrier per chunk.  Returns false (uniformly) if
+// a staging copy timed out; the caller must then stop using the shared
+// buffers.  The buffers may still be read by other threads when it returns:
+// the caller synchronises the CTA before the next unit.
 template <bool LINK, bool COHERENT>
 __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUtensorMap *map_r,
                                              const CUtensorMap *map_c, const LinkCoef *coef, FwdSmem &sm,
-                                             uint64_t *bar, int *s_ok, uint32_t (&ph)[2])
+                                             uint64_t *bar, uint32_t (&ph)[2])
 {
     const FwdUnit u = a.units[ui];
     const int t = threadIdx.x;
@@ -108,25 +110,15 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
     float acc = 0.0f;
     for (int c = 0; c < u.nchunks; ++c) {
         const int b = c & 1;
-        if (t == 0) {
-            // (ph indexed with constants so that it stays in registers)
-            const bool ok = mbar_wait(&bar[b], (b ? ph[1] : ph[0]) & 1u);
-            if (ok) {
-                if (b) ph[1] += 1;
-                else ph[0] += 1;
-            }
-            *s_ok = ok ? 1 : 0;
-            if (ok && c + 1 < u.nchunks) {
-                // the other buffer was last read before the barrier that ended
-                // chunk c - 1; order those reads before the async-proxy write
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                tma_box(sm.buf[b ^ 1], map, kst[c + 1] + kPad, (u.jc0 + c + 1) * kFC, &bar[b ^ 1]);
-            }
-        }
-        __syncthreads();
-        if (!*s_ok) {
-            // the copy of chunk c never completed: report, wait (bounded) for
-            // it once more so no copy lands after the buffers are released
+        // every thread waits for chunk c; the barrier then also tells that all
+        // threads are done with chunk c - 1, whose buffer the next copy reuses
+        // (ph indexed with constants so that it stays in registers)
+        bool ok = mbar_wait(&bar[b], (b ? ph[1] : ph[0]) & 1u);
+        ok = __syncthreads_and(ok) != 0;
+        if (!ok) {
+            // the copy of chunk c did not complete in time everywhere: report,
+            // wait (bounded) for it once more so no copy lands after the
+            // buffers are released
             if (t == 0) {
                 mbar_wait(&bar[b], (b ? ph[1] : ph[0]) & 1u);
                 if (a.err) {
@@ -135,6 +127,14 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
                 }
             }
             return false;
+        }
+        if (b) ph[1] += 1;
+        else ph[0] += 1;
+        if (t == 0 && c + 1 < u.nchunks) {
+            // the other buffer was last read in chunk c - 1 (before the
+            // barrier above); order those reads before the async-proxy write
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tma_box(sm.buf[b ^ 1], map, kst[c + 1] + kPad, (u.jc0 + c + 1) * kFC, &bar[b ^ 1]);
         }
         const int j0 = (u.jc0 + c) * kFC;
         const int ja = max(jlo, j0), jb = min(jhi, j0 + kFC - 1);
@@ -166,8 +166,8 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
                 di += 1.0f;
             }
         }
-        __syncthreads();
     }
+    // the caller synchronises the CTA before the buffers are used again
     if (!has_ray) return true;
     const float delta = a.delta[i];
     const float z = delta * acc;

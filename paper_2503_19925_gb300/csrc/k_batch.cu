@@ -48,7 +48,6 @@ struct __align__(128) BatchSmem {
     unsigned long long item;
     int ok;
     int go;
-    int s_ok;
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -162,7 +161,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
                 FwdArgs f = J.f;
                 f.img = J.img[q];
                 item_ok = forward_unit<true, true>(f, local, J.maps + 2 * q, J.maps + 2 * q + 1, J.coef, sm.u.fwd,
-                                                   sm.bar, &sm.s_ok, ph);
+                                                   sm.bar, ph);
             } else if (phase == 1 || phase == 3) {
                 AdjArgs a = J.a;
                 a.iter = round;

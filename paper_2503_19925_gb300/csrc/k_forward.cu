@@ -9,7 +9,9 @@
 // image read along that axis: x-driven rays read the column-major copy,
 // y-driven rays the row-major one.  Copies are double-buffered on two
 // mbarriers, so the copy of chunk c + 1 overlaps the samples of chunk c, and
-// each thread's two interpolation taps are shared-memory loads.  Out-of-range
+// each thread's two interpolation taps are shared-memory loads.  Every thread
+// waits on the mbarrier of its chunk; one CTA barrier per chunk then both
+// agrees on the outcome and frees the other buffer for the next copy.  Out-of-range
 // parts of a box are zero-filled by the copy, which is the projector's
 // zero-outside-the-image rule.  Every mbarrier wait is bounded: on a timeout the
 // CTA records EXACT_ERR_TIMEOUT, waits (bounded) for its copy in flight and
@@ -44,7 +46,6 @@ __global__ void __launch_bounds__(kFR) k_forward_tma(FwdArgs a, const __grid_con
     if (a.state && a.state->done) return;
     __shared__ __align__(128) FwdSmem sm;
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int s_ok;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0]);
         mbar_init(&bar[1]);
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kFR) k_forward_tma(FwdArgs a, const __grid_con
     }
     __syncthreads();
     uint32_t ph[2] = {0u, 0u};
-    forward_unit<LINK, false>(a, blockIdx.x, &map_r, &map_c, &coef, sm, bar, &s_ok, ph);
+    forward_unit<LINK, false>(a, blockIdx.x, &map_r, &map_c, &coef, sm, bar, ph);
 }
 
 // FP64 forward of the power iteration: z = inv_norm * A w, plus per-block
