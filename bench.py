@@ -229,14 +229,13 @@ def load_traffic(kernel: str):
     try:
         rec = json.load(open(path)).get(kernel)
         from paper_2503_19925_gb300 import _build
-        import glob
         import hashlib
         h = hashlib.sha256()
-        for src in sorted(glob.glob(os.path.join(_build.CSRC, "*"))):
-            h.update(open(src, "rb").read())
+        for src in rec["sources"]:  # the files the kernel is compiled from
+            h.update(open(os.path.join(_build.CSRC, src), "rb").read())
         if rec and rec.get("source_sha256") == h.hexdigest():
             return rec
-    except (OSError, ValueError):
+    except (OSError, ValueError, KeyError, TypeError):
         pass
     return None
 
