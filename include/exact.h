@@ -137,27 +137,50 @@ exact_status exact_adjoint(exact_plan_t plan, const float *r, float *g, exact_st
 exact_status exact_operator(exact_plan_t plan, const float *x, const void *y, exact_dtype y_dtype,
                             double I0, float *F, exact_stream_t stream);
 
+/* Stopping rules of exact_solve (see exact_solve_opts). */
+typedef enum {
+    EXACT_STOP_RESIDUAL = 0, /* relative change of the iterate */
+    EXACT_STOP_AVERAGE = 1   /* change of the running average of Sec. 3.1 */
+} exact_stop_rule;
+
 /* Options of exact_solve.  lo <= hi bound the box feasible set X = [lo, hi]^d
  * (lo = 0, hi = +inf is the nonnegative orthant of Sec. 3.1; lo = -inf
- * disables the lower bound).  If tol > 0 and check_every > 0 the solve stops
- * after the first iteration t that is a multiple of check_every with
- * rel_res = ||x_{t+1} - x_t|| / max(||x_t||, 1e-30) <= tol (FP64 norms).
- * average_tail != 0 returns the mean of the iterates x_{t+1} for
- * t >= floor(iters/2) instead of the last iterate (Sec. 3.1 averages the last
- * half of the iterates). */
+ * disables the lower bound).  Iterations are counted t = 1, 2, ...; x_t is the
+ * iterate after t of them.
+ *  - stop_rule EXACT_STOP_RESIDUAL: if tol > 0 and check_every > 0 the solve
+ *    stops after the first t that is a multiple of check_every with
+ *    rel_res = ||x_t - x_{t-1}|| / max(||x_{t-1}||, 1e-30) <= tol (FP64
+ *    norms).  average_tail != 0 returns the mean of x_t for
+ *    t > floor(iters/2) instead of the last iterate.
+ *  - stop_rule EXACT_STOP_AVERAGE (Sec. 3.1, comparison of methods): the
+ *    estimate at t is the mean xbar_t of the last m_t = max(1, floor(t/2))
+ *    iterates x_{t-m_t+1} .. x_t; if tol > 0 and check_every > 0 the solve
+ *    stops after the first t >= 2 that is a multiple of check_every with
+ *    avg_change = ||xbar_t - xbar_{t-1}|| <= tol (absolute, FP64; the paper
+ *    uses 1e-5), and returns xbar_T for the last iteration T run.  The running
+ *    sum is kept in FP64, so xbar_t is the exact mean of the FP32 iterates up
+ *    to one final rounding.  history: caller-owned device ring of history_cap
+ *    images [ny][nx] FP32 holding the iterates of the window; history_cap >=
+ *    max(1, floor(iters/2)).  average_tail must be 0. */
 typedef struct {
     double lo, hi, tol;
     int check_every;
     int average_tail;
+    int stop_rule;   /* exact_stop_rule */
+    int history_cap; /* EXACT_STOP_AVERAGE: images in history */
+    float *history;  /* EXACT_STOP_AVERAGE: device ring [history_cap][ny][nx] */
 } exact_solve_opts;
 
 typedef struct {
     int iters_done;      /* iterations run */
     double rel_res;      /* rel_res of the last iteration run (0 if none) */
     exact_status status; /* EXACT_OK or EXACT_ERR_NONFINITE */
+    double avg_change;   /* EXACT_STOP_AVERAGE: ||xbar_T - xbar_{T-1}|| of the last
+                          * iteration T run (0 if T < 2); else 0 */
 } exact_solve_info;
 
-/* Default options: lo = 0, hi = +inf, tol = 0, check_every = 1, average_tail = 0. */
+/* Default options: lo = 0, hi = +inf, tol = 0, check_every = 1, average_tail = 0,
+ * stop_rule = EXACT_STOP_RESIDUAL, no history. */
 exact_solve_opts exact_solve_opts_default(void);
 
 /* Projected extragradient, Eq. (11), with constant step eta:
@@ -234,7 +257,8 @@ typedef struct exact_batch *exact_batch_t;
 /* One reconstruction of a batch: a plan with its bound workspace (each job
  * needs its own plan and workspace), device counts y as in exact_operator, the
  * source intensity, the step, the iteration count, the options (average_tail
- * must be 0), the device image x (x_1 in, result out) and an optional host
+ * must be 0 and stop_rule EXACT_STOP_RESIDUAL, else EXACT_ERR_UNSUPPORTED), the
+ * device image x (x_1 in, result out) and an optional host
  * info struct written when the stream reaches the end of the batch. */
 typedef struct {
     exact_plan_t plan;

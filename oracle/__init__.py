@@ -249,6 +249,63 @@ def solve(g: Geometry, S, mu, I0: float, y, eta: float, iters: int, x1=None,
     return SolveResult(x, done, hist[:done], avg)
 
 
+def window_size(t: int) -> int:
+    """Iterates in the running average at iteration t >= 1.  Sec. 3.1
+    averages "the previous t/2 iterates"; read as floor(t/2), and at least
+    one so that the average exists from the first iteration."""
+    return max(1, t // 2)
+
+
+def running_averages(iterates):
+    """xbar_t for t = 1 .. T of the iterate sequence [x_1, ..., x_T]: the plain
+    mean of x_{t-m+1} .. x_t with m = window_size(t) (brute force, FP64)."""
+    xs = [np.asarray(v, dtype=np.float64) for v in iterates]
+    out = []
+    for t in range(1, len(xs) + 1):
+        m = window_size(t)
+        out.append(sum(xs[t - m:t]) / m)
+    return out
+
+
+@dataclass
+class WindowSolveResult:
+    x_avg: np.ndarray        # xbar_T
+    iters: int               # T
+    changes: np.ndarray      # ||xbar_t - xbar_{t-1}|| for t = 2 .. T
+    x_last: np.ndarray       # x_T
+
+
+def solve_running_average(g: Geometry, S, mu, I0: float, y, eta: float, iters: int, tol: float,
+                          check_every: int = 1, x1=None, lo: float = 0.0, hi: float = np.inf,
+                          bg=None) -> WindowSolveResult:
+    """Projected extragradient (Eq. (11)) with the stopping rule of Sec. 3.1:
+    stop after the first iteration t >= 2 (a multiple of check_every) with
+    ||xbar_t - xbar_{t-1}||_2 <= tol, where xbar_t is the running average of
+    window_size(t) iterates; return xbar_T.  x1 (default 0) is projected onto
+    the box first.  Each step calls the C operator; the window is kept as a
+    list of the FP64 iterates and averaged directly."""
+    S, mu, y = _f64(S), _f64(mu), _f64(y)
+    x = np.zeros((g.ny, g.nx)) if x1 is None else _f64(x1).reshape(g.ny, g.nx).copy()
+    x = np.clip(x, lo, hi)
+    window, changes = [], []
+    prev = None
+    xbar = x.copy()
+    t = 0
+    for t in range(1, iters + 1):
+        xh = np.clip(x - eta * operator(g, x, S, mu, I0, y, bg), lo, hi)
+        x = np.clip(x - eta * operator(g, xh, S, mu, I0, y, bg), lo, hi)
+        window.append(x.copy())
+        m = window_size(t)
+        del window[:-m]
+        xbar = sum(window) / m
+        if prev is not None:
+            changes.append(float(np.linalg.norm(xbar - prev)))
+            if tol > 0.0 and check_every > 0 and t % check_every == 0 and changes[-1] <= tol:
+                break
+        prev = xbar
+    return WindowSolveResult(xbar, t, np.array(changes), x)
+
+
 def norm_estimate(g: Geometry, max_iters: int = 500, rtol: float = 1e-9):
     """Power-iteration estimate of ||A||_op^2; returns (lam, iterations)."""
     lib = _load()

@@ -360,7 +360,7 @@ size_t carve(Plan &P, char *base)
     const int nb_fwd = forward_d_blocks(P.n);
     const int nb_adj_d = adjoint_d_blocks(P.g.nx, P.g.ny);
     const int nb_d = nb_adj_d > kSumsqParts ? nb_adj_d : kSumsqParts;
-    P.partials = c.take<double>(base, (size_t)(2 * nb_adj + (nb_fwd > kSumsqParts ? nb_fwd : kSumsqParts) + nb_d));
+    P.partials = c.take<double>(base, (size_t)(kPartStride * nb_adj + (nb_fwd > kSumsqParts ? nb_fwd : kSumsqParts) + nb_d));
     P.avg = c.take<double>(base, (size_t)P.d);
     P.xrd = c.take<double>(base, (size_t)(ny * P.ldr()));
     P.xcd = c.take<double>(base, (size_t)(nx * P.ldc()));
@@ -386,6 +386,7 @@ void info_copy_cb(void *data)
     c->dst->iters_done = c->src->iters_done;
     c->dst->rel_res = c->src->rel_res;
     c->dst->status = (exact_status)c->src->status;
+    c->dst->avg_change = c->src->avg_change;
     if (c->one_shot) delete c;
 }
 
@@ -502,6 +503,9 @@ exact_solve_opts exact_solve_opts_default(void)
     o.tol = 0.0;
     o.check_every = 1;
     o.average_tail = 0;
+    o.stop_rule = EXACT_STOP_RESIDUAL;
+    o.history_cap = 0;
+    o.history = nullptr;
     return o;
 }
 
@@ -807,6 +811,10 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     if (isnan(o.lo) || isnan(o.hi) || o.lo > o.hi || o.lo == INFINITY || o.hi == -INFINITY)
         return EXACT_ERR_INVALID_ARG;
     if (!isfin(o.tol) || o.tol < 0.0 || o.check_every < 0) return EXACT_ERR_INVALID_ARG;
+    if (o.stop_rule != EXACT_STOP_RESIDUAL && o.stop_rule != EXACT_STOP_AVERAGE) return EXACT_ERR_INVALID_ARG;
+    const bool running = o.stop_rule == EXACT_STOP_AVERAGE;
+    if (running && (o.average_tail || !o.history || o.history_cap < (iters / 2 > 1 ? iters / 2 : 1)))
+        return EXACT_ERR_INVALID_ARG;
     Plan &P = *reinterpret_cast<Plan *>(plan);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const float lo = (float)o.lo, hi = (float)o.hi;
@@ -819,7 +827,7 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     EXACT_TRY(launch_pack(x, P.xr[0], P.xc[0], P.g.nx, P.g.ny, P.ldr(), P.ldc(), lo, hi, true, s));
     EXACT_TRY(cudaMemsetAsync(P.xr[1], 0, sizeof(float) * (size_t)(P.g.ny * P.ldr()), s));
     EXACT_TRY(cudaMemsetAsync(P.xc[1], 0, sizeof(float) * (size_t)(P.g.nx * P.ldc()), s));
-    if (o.average_tail) EXACT_TRY(cudaMemsetAsync(P.avg, 0, sizeof(double) * (size_t)P.d, s));
+    if (o.average_tail || running) EXACT_TRY(cudaMemsetAsync(P.avg, 0, sizeof(double) * (size_t)P.d, s));
 
     FwdArgs f;
     memset(&f, 0, sizeof(f));
@@ -854,9 +862,11 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     a.lo = lo;
     a.hi = hi;
     a.partials = P.partials;
-    a.avg = o.average_tail ? P.avg : nullptr;
+    a.avg = (o.average_tail || running) ? P.avg : nullptr;
     a.avg_from = avg_from;
     a.state = P.state;
+    a.hist = running ? o.history : nullptr;
+    a.hist_drop = -1;
     const bool fan = P.g.beam == 1;
     int u;
     for (int t = 0; t < iters; ++t) {
@@ -878,15 +888,24 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
         prof_end(P, u, s);
         a.out_r = P.xr[0];
         a.out_c = P.xc[0];
+        if (running) {
+            // iterate number it = t + 1 enters the window of the last
+            // m = max(1, floor(it/2)); when m did not grow, x_{it-m} leaves it
+            const int it = t + 1, m = it / 2 > 1 ? it / 2 : 1, mp = (it - 1) / 2 > 1 ? (it - 1) / 2 : 1;
+            a.hist_put = it % o.history_cap;
+            a.hist_drop = (it >= 2 && m == mp) ? (it - m) % o.history_cap : -1;
+            a.inv_m = 1.0 / (double)m;
+            a.inv_m_prev = it >= 2 ? 1.0 / (double)mp : 0.0;
+        }
         u = prof_begin(P, 2, t, s);
         EXACT_TRY(launch_adjoint(a, ADJ_EG_FINAL, fan, s));
         prof_end(P, u, s);
         u = prof_begin(P, 3, t, s);
-        EXACT_TRY(launch_solve_reduce(P.partials, nb, P.state, t, o.tol, o.check_every, s));
+        EXACT_TRY(launch_solve_reduce(P.partials, nb, P.state, t, o.tol, o.check_every, o.stop_rule, s));
         prof_end(P, u, s);
     }
-    EXACT_TRY(launch_unpack(P.xr[0], P.ldr(), P.g.nx, P.g.ny, x, o.average_tail ? P.avg : nullptr, P.state,
-                            avg_from, s));
+    EXACT_TRY(launch_unpack(P.xr[0], P.ldr(), P.g.nx, P.g.ny, x, (o.average_tail || running) ? P.avg : nullptr,
+                            P.state, running ? -1 : avg_from, s));
     if (info) {
         st = enqueue_info(P.state, P.host_state, info, P.captured_infos, s);
         if (st != EXACT_OK) return st;
@@ -905,7 +924,7 @@ exact_status exact_norm_estimate(exact_plan_t plan, int max_iters, double rtol, 
     const int nb_adj = adjoint_blocks(P.g.nx, P.g.ny);
     const int nb_fwd = forward_d_blocks(P.n);
     const int nb_adj_d = adjoint_d_blocks(P.g.nx, P.g.ny);
-    double *pz = P.partials + 2 * nb_adj;
+    double *pz = P.partials + kPartStride * nb_adj;
     double *pw = pz + nb_fwd;
     const bool fan = P.g.beam == 1;
     EXACT_TRY(launch_power_init(P.xrd, P.xcd, P.g.nx, P.g.ny, P.ldr(), P.ldc(), P.state, s));
@@ -938,7 +957,7 @@ exact_status exact_norm_estimate_f32(exact_plan_t plan, int max_iters, double rt
     Plan &P = *reinterpret_cast<Plan *>(plan);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int nb_adj = adjoint_blocks(P.g.nx, P.g.ny);
-    double *pz = P.partials + 2 * nb_adj;
+    double *pz = P.partials + kPartStride * nb_adj;
     double *pw = pz + (forward_d_blocks(P.n) > kSumsqParts ? forward_d_blocks(P.n) : kSumsqParts);
     EXACT_TRY(launch_power_init_f(P.w32, P.d, P.state, s));
     FwdArgs f;
@@ -1196,7 +1215,7 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
         if (isnan(o.lo) || isnan(o.hi) || o.lo > o.hi || o.lo == INFINITY || o.hi == -INFINITY)
             return EXACT_ERR_INVALID_ARG;
         if (!isfin(o.tol) || o.tol < 0.0 || o.check_every < 0) return EXACT_ERR_INVALID_ARG;
-        if (o.average_tail) return EXACT_ERR_UNSUPPORTED;
+        if (o.average_tail || o.stop_rule != EXACT_STOP_RESIDUAL) return EXACT_ERR_UNSUPPORTED;
         for (int q = 0; q < j; ++q)
             if (jobs[q].plan == J.plan) return EXACT_ERR_INVALID_ARG;
         rounds = J.iters > rounds ? J.iters : rounds;

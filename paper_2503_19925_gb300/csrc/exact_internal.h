@@ -98,7 +98,12 @@ struct DevState {
     double lam;       // power iteration: latest ||A v||^2
     double lam_prev;
     double inv_norm;  // power iteration: 1/||w|| for the next forward
+    double avg_change;  // running-average rule: ||xbar_t - xbar_{t-1}||
 };
+
+// FP64 partial sums per adjoint tile of the full step: ||x_out - x_base||^2,
+// ||x_base||^2 and ||xbar_t - xbar_{t-1}||^2 (running-average rule).
+constexpr int kPartStride = 3;
 
 struct Plan {
     exact_geometry g;
@@ -206,6 +211,13 @@ struct AdjArgs {
     double *avg;           // EG_FINAL: tail-average accumulator or null
     int avg_from;          // EG_FINAL: accumulate when iteration index >= avg_from
     int iter;              // iteration index of this launch
+    // EG_FINAL, running-average rule (null hist: off).  avg holds the FP64
+    // window sum; hist the ring of window iterates [cap][ny][nx]; this launch
+    // stores x_out in slot hist_put and removes slot hist_drop (-1: none)
+    // from the sum; the partials get ||sum / m - sum_prev / m_prev||^2.
+    float *hist;
+    int hist_put, hist_drop;
+    double inv_m, inv_m_prev;
     const DevState *state;
 };
 
@@ -246,7 +258,7 @@ cudaError_t launch_unpack(const float *xr, long long ldr, int nx, int ny, float 
                           const DevState *state, int avg_from, cudaStream_t s);
 cudaError_t launch_collapse(const void *y, int dtype, int W, long long n, float *Y, cudaStream_t s);
 cudaError_t launch_solve_reduce(const double *partials, int nparts, DevState *st, int iter, double tol,
-                                int check_every, cudaStream_t s);
+                                int check_every, int rule, cudaStream_t s);
 cudaError_t launch_reset_state(DevState *st, cudaStream_t s);
 
 // FP64 power iteration pieces

@@ -210,7 +210,7 @@ struct AdjSmem {
     float acc[G][2][kRows * kAccLd];  // per warp: x-driven then y-driven accumulators
     float stage[kTH][kTW + 1];
     float tile[kTH][kTW + 1];
-    double red0[G], red1[G];
+    double red0[G], red1[G], red2[G];
 };
 
 // Bin range of the rays that cross the segment between two points whose
@@ -327,7 +327,7 @@ __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, l
         sm.stage[rl][k] = s;
     }
     __syncthreads();
-    double s0 = 0.0, s1 = 0.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
         const int px = t % kTW, py = t / kTW;
         float gsum = sm.stage[py][px];
@@ -346,7 +346,21 @@ __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, l
             if (inside) a.out_r[pr] = xn;
             sm.tile[py][px] = xn;
             if (MODE == ADJ_EG_FINAL && inside) {
-                if (a.avg && a.iter >= a.avg_from) a.avg[(long long)ky * a.nx + kx] += (double)xn;
+                const long long q = (long long)ky * a.nx + kx;
+                if (a.hist) {
+                    // running average of Sec. 3.1: window sum in FP64 (exact
+                    // for FP32 summands), ring of the window's iterates
+                    const long long dpix = (long long)a.nx * a.ny;
+                    const double sp = a.avg[q];
+                    double sn = sp + (double)xn;
+                    if (a.hist_drop >= 0) sn -= (double)a.hist[(long long)a.hist_drop * dpix + q];
+                    a.hist[(long long)a.hist_put * dpix + q] = xn;
+                    a.avg[q] = sn;
+                    const double dv = sn * a.inv_m - sp * a.inv_m_prev;
+                    s2 += dv * dv;
+                } else if (a.avg && a.iter >= a.avg_from) {
+                    a.avg[q] += (double)xn;
+                }
                 const double dd = (double)xn - (double)xb;
                 s0 += dd * dd;
                 s1 += (double)xb * (double)xb;
@@ -365,20 +379,24 @@ __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, l
         for (int o = 16; o > 0; o >>= 1) {
             s0 += __shfl_down_sync(0xffffffffu, s0, o);
             s1 += __shfl_down_sync(0xffffffffu, s1, o);
+            s2 += __shfl_down_sync(0xffffffffu, s2, o);
         }
         if (lane == 0) {
             sm.red0[g] = s0;
             sm.red1[g] = s1;
+            sm.red2[g] = s2;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double t0 = 0.0, t1 = 0.0;
+            double t0 = 0.0, t1 = 0.0, t2 = 0.0;
             for (int q = 0; q < G; ++q) {
                 t0 += sm.red0[q];
                 t1 += sm.red1[q];
+                t2 += sm.red2[q];
             }
-            a.partials[2 * blk] = t0;
-            a.partials[2 * blk + 1] = t1;
+            a.partials[kPartStride * blk] = t0;
+            a.partials[kPartStride * blk + 1] = t1;
+            a.partials[kPartStride * blk + 2] = t2;
         }
     }
 }

@@ -66,8 +66,8 @@ __device__ void batch_reduce(const BatchJob &J, int iter, double *scratch)
     const int nparts = J.tiles_x * J.tiles_y;
     double s0 = 0.0, s1 = 0.0;
     for (int i = threadIdx.x; i < nparts; i += kBatchThreads) {
-        s0 += __ldcg(J.a.partials + 2 * i);
-        s1 += __ldcg(J.a.partials + 2 * i + 1);
+        s0 += __ldcg(J.a.partials + kPartStride * i);
+        s1 += __ldcg(J.a.partials + kPartStride * i + 1);
     }
     scratch[threadIdx.x] = s0;
     scratch[kBatchThreads + threadIdx.x] = s1;

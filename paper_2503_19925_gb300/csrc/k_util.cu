@@ -62,7 +62,10 @@ __global__ void k_unpack(const float *xr, long long ldr, int nx, int ny, float *
 {
     const long long d = (long long)nx * ny;
     long long cnt = 0;
-    if (avg) cnt = (long long)st->iters_done - avg_from;
+    // avg_from >= 0: tail average of the iterates after avg_from; avg_from < 0:
+    // running-average window sum of the last max(1, floor(T/2)) iterates
+    if (avg) cnt = avg_from >= 0 ? (long long)st->iters_done - avg_from : max(1, st->iters_done / 2);
+    if (avg && avg_from < 0 && st->iters_done == 0) cnt = 0;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < d;
          p += (long long)gridDim.x * blockDim.x) {
         const long long j = p / nx, k = p - j * nx;
@@ -112,19 +115,24 @@ __device__ double block_sum_fixed(const double *src, int count, int stride)
 }
 
 __global__ void __launch_bounds__(RT) k_solve_reduce(const double *partials, int nparts, DevState *st, int iter,
-                                                     double tol, int check_every)
+                                                     double tol, int check_every, int rule)
 {
     if (st->done) return;
-    const double num = block_sum_fixed(partials, nparts, 2);
-    const double den = block_sum_fixed(partials + 1, nparts, 2);
+    const double num = block_sum_fixed(partials, nparts, kPartStride);
+    const double den = block_sum_fixed(partials + 1, nparts, kPartStride);
+    const double chg = rule == EXACT_STOP_AVERAGE ? block_sum_fixed(partials + 2, nparts, kPartStride) : 0.0;
     if (threadIdx.x == 0) {
         const double rel = sqrt(num) / fmax(sqrt(den), 1e-30);
+        const int t = iter + 1;  // iterations run
         st->rel_res = rel;
-        st->iters_done = iter + 1;
-        if (!isfinite(rel)) {
+        st->avg_change = (rule == EXACT_STOP_AVERAGE && t >= 2) ? sqrt(chg) : 0.0;
+        st->iters_done = t;
+        const double crit = rule == EXACT_STOP_AVERAGE ? st->avg_change : rel;
+        const bool may_stop = rule == EXACT_STOP_AVERAGE ? t >= 2 : true;
+        if (!isfinite(rel) || !isfinite(crit)) {
             st->status = EXACT_ERR_NONFINITE;
             st->done = 1;
-        } else if (tol > 0.0 && check_every > 0 && (iter + 1) % check_every == 0 && rel <= tol) {
+        } else if (may_stop && tol > 0.0 && check_every > 0 && t % check_every == 0 && crit <= tol) {
             st->done = 1;
         }
     }
@@ -139,6 +147,7 @@ __global__ void k_reset_state(DevState *st)
     st->lam = 0.0;
     st->lam_prev = 0.0;
     st->inv_norm = 1.0;
+    st->avg_change = 0.0;
 }
 
 __global__ void k_power_init(double *xrd, double *xcd, int nx, int ny, long long ldr, long long ldc, DevState *st)
@@ -268,9 +277,9 @@ cudaError_t launch_collapse(const void *y, int dtype, int W, long long n, float 
 }
 
 cudaError_t launch_solve_reduce(const double *partials, int nparts, DevState *st, int iter, double tol,
-                                int check_every, cudaStream_t s)
+                                int check_every, int rule, cudaStream_t s)
 {
-    k_solve_reduce<<<1, RT, 0, s>>>(partials, nparts, st, iter, tol, check_every);
+    k_solve_reduce<<<1, RT, 0, s>>>(partials, nparts, st, iter, tol, check_every, rule);
     return cudaGetLastError();
 }
 

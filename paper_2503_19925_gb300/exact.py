@@ -47,11 +47,16 @@ class _Windows(ctypes.Structure):
 
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_double), ("hi", ctypes.c_double), ("tol", ctypes.c_double),
-                ("check_every", ctypes.c_int), ("average_tail", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("average_tail", ctypes.c_int), ("stop_rule", ctypes.c_int),
+                ("history_cap", ctypes.c_int), ("history", ctypes.c_void_p)]
 
 
 class _SolveInfo(ctypes.Structure):
-    _fields_ = [("iters_done", ctypes.c_int), ("rel_res", ctypes.c_double), ("status", ctypes.c_int)]
+    _fields_ = [("iters_done", ctypes.c_int), ("rel_res", ctypes.c_double), ("status", ctypes.c_int),
+                ("avg_change", ctypes.c_double)]
+
+
+STOP_RULES = {"residual": 0, "average": 1}
 
 
 class _Job(ctypes.Structure):
@@ -157,6 +162,7 @@ class SolveInfo:
     iters_done: int
     rel_res: float
     status: int
+    avg_change: float = 0.0
 
 
 class Plan:
@@ -250,15 +256,26 @@ class Plan:
 
     def solve(self, y: torch.Tensor, I0: float, eta: float, iters: int, x: torch.Tensor | None = None,
               lo: float = 0.0, hi: float = math.inf, tol: float = 0.0, check_every: int = 1,
-              average_tail: bool = False, sync: bool = True):
-        """Run ``iters`` extragradient iterations in place on ``x`` (zeros if
-        None).  Returns (x, SolveInfo); with sync=False the info is filled
-        once the current stream reaches the end of the solve."""
+              average_tail: bool = False, stop_rule: str = "residual", sync: bool = True):
+        """Run up to ``iters`` extragradient iterations in place on ``x``
+        (zeros if None).  stop_rule "residual" tests the relative change of the
+        iterate, "average" the change of the running average of the last half
+        of the iterates (and returns that average; its window ring is
+        allocated here).  Returns (x, SolveInfo); with sync=False the info is
+        filled once the current stream reaches the end of the solve."""
         dt = self._y(y)
         if x is None:
             x = torch.zeros(self.shape_img, dtype=torch.float32, device=self.device)
         self._t(x, self.shape_img, name="x")
-        opts = _SolveOpts(float(lo), float(hi), float(tol), int(check_every), int(bool(average_tail)))
+        if stop_rule not in STOP_RULES:
+            raise ValueError(f"stop_rule must be one of {sorted(STOP_RULES)}")
+        hist = None
+        if stop_rule == "average":
+            cap = max(1, int(iters) // 2)
+            hist = torch.empty((cap,) + tuple(self.shape_img), dtype=torch.float32, device=self.device)
+        opts = _SolveOpts(float(lo), float(hi), float(tol), int(check_every), int(bool(average_tail)),
+                          STOP_RULES[stop_rule], 0 if hist is None else hist.shape[0],
+                          None if hist is None else hist.data_ptr())
         info = _SolveInfo()
         _check("exact_solve", load().exact_solve(self._h, _ptr(y), dt, float(I0), float(eta), int(iters),
                                                  ctypes.byref(opts), _ptr(x), ctypes.byref(info), _stream()))
@@ -267,7 +284,7 @@ class Plan:
         done = torch.cuda.Event()
         done.record()
         self._pending = [(e, i) for e, i in getattr(self, "_pending", []) if not e.query()]
-        self._pending.append((done, info))
+        self._pending.append((done, (info, hist)))
         if sync:
             done.synchronize()
         return x, info
@@ -397,7 +414,7 @@ class Batch:
             p._t(x, p.shape_img, name="x")
             xs.append(x)
             arr[k] = _Job(p._h.value, jb.y.data_ptr(), dt, float(jb.I0), float(jb.eta), int(jb.iters),
-                          _SolveOpts(float(jb.lo), float(jb.hi), float(jb.tol), int(jb.check_every), 0),
+                          _SolveOpts(float(jb.lo), float(jb.hi), float(jb.tol), int(jb.check_every), 0, 0, 0, None),
                           x.data_ptr(), ctypes.pointer(infos[k]))
         _check("exact_batch_solve", load().exact_batch_solve(self._h, arr, n, _stream()))
         if torch.cuda.is_current_stream_capturing():
