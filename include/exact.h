@@ -137,6 +137,48 @@ exact_status exact_adjoint(exact_plan_t plan, const float *r, float *g, exact_st
 exact_status exact_operator(exact_plan_t plan, const float *x, const void *y, exact_dtype y_dtype,
                             double I0, float *F, exact_stream_t stream);
 
+/* Options of the projection onto the TV ball intersected with a box (Sec. 3.1,
+ * implementation of projections): Dykstra's algorithm between
+ * X1 = {x : ||x||_TV <= tau} and X2 = [lo, hi]^d, P_X1 approximated by the
+ * TV-regularised problem argmin_x ||x - z||^2 + lam ||x||_TV with lam found by
+ * bisection.  ||x||_TV is the isotropic total variation with forward
+ * differences (zero past the last row and column); the regularised problem is
+ * solved by fgp_iters steps of the fast gradient projection method on its
+ * dual, warm-started from the previous solve of the same projection. */
+typedef struct {
+    int fgp_iters;      /* dual steps per regularised solve (default 40) */
+    int max_bisect;     /* regularised solves per projection onto X1 (default 40) */
+    int max_dykstra;    /* Dykstra rounds (default 50) */
+    int pad;
+    double tol_tv;      /* accept lam once | ||x||_TV - tau | <= tol_tv (default 0.01, Sec. 3.1) */
+    double tol_dykstra; /* stop Dykstra once ||z_{k+1} - z_k|| <= tol_dykstra (default 1e-4, Sec. 3.1) */
+    double lam0;        /* first lam of the bisection (<= 0: 1) */
+} exact_tv_opts;
+
+typedef struct {
+    int rounds;          /* Dykstra rounds run */
+    int solves;          /* regularised solves run */
+    double lam;          /* lam of the last regularised solve */
+    exact_status status; /* EXACT_OK or EXACT_ERR_TIMEOUT */
+} exact_tv_info;
+
+exact_tv_opts exact_tv_opts_default(void);
+
+/* Device workspace exact_tv_project needs for an nx x ny image (about 52 bytes
+ * per pixel).  0 if no CUDA device is current. */
+size_t exact_tv_workspace_bytes(int nx, int ny);
+
+/* x = P_X(z) for X = {||x||_TV <= tau} ∩ [lo, hi]^d (Sec. 3.1; the paper uses
+ * the nonnegative orthant lo = 0, hi = +inf and tau = ||x_star||_TV).  z, x:
+ * device [ny][nx] FP32 (distinct buffers); tau >= 0; lo <= hi; workspace:
+ * device memory of at least exact_tv_workspace_bytes(nx, ny), caller-owned;
+ * opts NULL means the defaults; info may be NULL.  One cooperative launch on
+ * `stream`; synchronises the stream and returns EXACT_ERR_TIMEOUT if a grid
+ * barrier of the launch gave up waiting (x is then not valid). */
+exact_status exact_tv_project(int nx, int ny, const float *z, double tau, double lo, double hi,
+                              const exact_tv_opts *opts, float *x, void *workspace, size_t workspace_bytes,
+                              exact_tv_info *info, exact_stream_t stream);
+
 /* Stopping rules of exact_solve (see exact_solve_opts). */
 typedef enum {
     EXACT_STOP_RESIDUAL = 0, /* relative change of the iterate */
@@ -145,8 +187,12 @@ typedef enum {
 
 /* Options of exact_solve.  lo <= hi bound the box feasible set X = [lo, hi]^d
  * (lo = 0, hi = +inf is the nonnegative orthant of Sec. 3.1; lo = -inf
- * disables the lower bound).  Iterations are counted t = 1, 2, ...; x_t is the
- * iterate after t of them.
+ * disables the lower bound); tv_bound > 0 intersects it with the TV ball of
+ * Sec. 3.1 (each half and full step then projects with exact_tv_project's
+ * algorithm, the bisection of each of the two projections starting from its
+ * lam of the previous iteration; only stop_rule EXACT_STOP_RESIDUAL without
+ * average_tail, else EXACT_ERR_UNSUPPORTED).  Iterations are counted
+ * t = 1, 2, ...; x_t is the iterate after t of them.
  *  - stop_rule EXACT_STOP_RESIDUAL: if tol > 0 and check_every > 0 the solve
  *    stops after the first t that is a multiple of check_every with
  *    rel_res = ||x_t - x_{t-1}|| / max(||x_{t-1}||, 1e-30) <= tol (FP64
@@ -169,6 +215,8 @@ typedef struct {
     int stop_rule;   /* exact_stop_rule */
     int history_cap; /* EXACT_STOP_AVERAGE: images in history */
     float *history;  /* EXACT_STOP_AVERAGE: device ring [history_cap][ny][nx] */
+    double tv_bound; /* > 0: X = {||x||_TV <= tv_bound} ∩ [lo, hi]^d (see exact_tv_project) */
+    exact_tv_opts tv; /* options of that projection */
 } exact_solve_opts;
 
 typedef struct {
@@ -180,7 +228,8 @@ typedef struct {
 } exact_solve_info;
 
 /* Default options: lo = 0, hi = +inf, tol = 0, check_every = 1, average_tail = 0,
- * stop_rule = EXACT_STOP_RESIDUAL, no history. */
+ * stop_rule = EXACT_STOP_RESIDUAL, no history, tv_bound = 0 (no TV ball),
+ * tv = exact_tv_opts_default(). */
 exact_solve_opts exact_solve_opts_default(void);
 
 /* Projected extragradient, Eq. (11), with constant step eta:

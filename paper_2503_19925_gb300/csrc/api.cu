@@ -360,13 +360,18 @@ size_t carve(Plan &P, char *base)
     const int nb_fwd = forward_d_blocks(P.n);
     const int nb_adj_d = adjoint_d_blocks(P.g.nx, P.g.ny);
     const int nb_d = nb_adj_d > kSumsqParts ? nb_adj_d : kSumsqParts;
-    P.partials = c.take<double>(base, (size_t)(kPartStride * nb_adj + (nb_fwd > kSumsqParts ? nb_fwd : kSumsqParts) + nb_d));
+    P.tv_grid = tv_grid(P.d);
+    const int nb_eg = nb_adj > P.tv_grid ? nb_adj : P.tv_grid;  // partial-norm producers of a full step
+    P.partials = c.take<double>(base, (size_t)(kPartStride * nb_eg + (nb_fwd > kSumsqParts ? nb_fwd : kSumsqParts) + nb_d));
     P.avg = c.take<double>(base, (size_t)P.d);
     P.xrd = c.take<double>(base, (size_t)(ny * P.ldr()));
     P.xcd = c.take<double>(base, (size_t)(nx * P.ldc()));
     P.zd = c.take<double>(base, (size_t)P.n);
     P.w32 = c.take<float>(base, (size_t)P.d);
     P.state = c.take<DevState>(base, 1);
+    P.tv_step = c.take<float>(base, (size_t)P.d);
+    P.tv_lam = c.take<double>(base, 2);
+    if (P.tv_grid > 0) P.tv_ws = c.take<char>(base, tv_workspace_bytes(nx, ny, P.tv_grid));
     return c.off;
 }
 
@@ -506,6 +511,8 @@ exact_solve_opts exact_solve_opts_default(void)
     o.stop_rule = EXACT_STOP_RESIDUAL;
     o.history_cap = 0;
     o.history = nullptr;
+    o.tv_bound = 0.0;
+    o.tv = exact_tv_opts_default();
     return o;
 }
 
@@ -815,7 +822,14 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     const bool running = o.stop_rule == EXACT_STOP_AVERAGE;
     if (running && (o.average_tail || !o.history || o.history_cap < (iters / 2 > 1 ? iters / 2 : 1)))
         return EXACT_ERR_INVALID_ARG;
+    if (isnan(o.tv_bound) || o.tv_bound < 0.0 || o.tv_bound == INFINITY) return EXACT_ERR_INVALID_ARG;
+    const bool tvb = o.tv_bound > 0.0;
+    if (tvb && (o.tv.fgp_iters < 1 || o.tv.max_bisect < 1 || o.tv.max_dykstra < 0 || !(o.tv.tol_tv >= 0.0) ||
+                !(o.tv.tol_dykstra >= 0.0) || isnan(o.tv.lam0) || o.tv.lam0 == INFINITY))
+        return EXACT_ERR_INVALID_ARG;
+    if (tvb && (running || o.average_tail)) return EXACT_ERR_UNSUPPORTED;
     Plan &P = *reinterpret_cast<Plan *>(plan);
+    if (tvb && !P.tv_ws) return EXACT_ERR_CUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const float lo = (float)o.lo, hi = (float)o.hi;
     const LinkCoef coef = make_coef(P, I0);
@@ -828,6 +842,28 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     EXACT_TRY(cudaMemsetAsync(P.xr[1], 0, sizeof(float) * (size_t)(P.g.ny * P.ldr()), s));
     EXACT_TRY(cudaMemsetAsync(P.xc[1], 0, sizeof(float) * (size_t)(P.g.nx * P.ldc()), s));
     if (o.average_tail || running) EXACT_TRY(cudaMemsetAsync(P.avg, 0, sizeof(double) * (size_t)P.d, s));
+    TvLaunch tvl;
+    memset(&tvl, 0, sizeof(tvl));
+    if (tvb) {
+        const double lam2[2] = {o.tv.lam0, o.tv.lam0};
+        EXACT_TRY(cudaMemcpyAsync(P.tv_lam, lam2, sizeof(lam2), cudaMemcpyHostToDevice, s));
+        tvl.nx = P.g.nx;
+        tvl.ny = P.g.ny;
+        tvl.grid = P.tv_grid;
+        tvl.z = P.tv_step;
+        tvl.ldr = P.ldr();
+        tvl.ldc = P.ldc();
+        tvl.ws = P.tv_ws;
+        tvl.state = P.state;
+        tvl.tau = o.tv_bound;
+        tvl.tol_tv = o.tv.tol_tv;
+        tvl.tol_dykstra = o.tv.tol_dykstra;
+        tvl.fgp_iters = o.tv.fgp_iters;
+        tvl.max_bisect = o.tv.max_bisect;
+        tvl.max_dykstra = o.tv.max_dykstra;
+        tvl.lo = lo;
+        tvl.hi = hi;
+    }
 
     FwdArgs f;
     memset(&f, 0, sizeof(f));
@@ -879,7 +915,18 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
         a.out_c = P.xc[1];
         a.iter = t;
         u = prof_begin(P, 1, t, s);
-        EXACT_TRY(launch_adjoint(a, ADJ_EG, fan, s));
+        if (tvb) {
+            // unprojected half step, then its projection onto the TV ball ∩ box
+            a.out = P.tv_step;
+            EXACT_TRY(launch_adjoint(a, ADJ_STEP, fan, s));
+            tvl.out_r = P.xr[1];
+            tvl.out_c = P.xc[1];
+            tvl.old_r = nullptr;
+            tvl.lam_io = P.tv_lam;
+            EXACT_TRY(launch_tv_project(tvl, s));
+        } else {
+            EXACT_TRY(launch_adjoint(a, ADJ_EG, fan, s));
+        }
         prof_end(P, u, s);
         // full step from the same base: x_{t+1} = P(x_t - eta F(x_{t+1/2}))
         f.img = img_of(P, 1);
@@ -898,10 +945,24 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
             a.inv_m_prev = it >= 2 ? 1.0 / (double)mp : 0.0;
         }
         u = prof_begin(P, 2, t, s);
-        EXACT_TRY(launch_adjoint(a, ADJ_EG_FINAL, fan, s));
+        if (tvb) {
+            // unprojected full step from x_t, projected into x_t's padded
+            // copies (each pixel's old value is read first for the norms)
+            a.out = P.tv_step;
+            EXACT_TRY(launch_adjoint(a, ADJ_STEP, fan, s));
+            tvl.out_r = P.xr[0];
+            tvl.out_c = P.xc[0];
+            tvl.old_r = P.xr[0];
+            tvl.norm_part = P.partials;
+            tvl.lam_io = P.tv_lam + 1;
+            EXACT_TRY(launch_tv_project(tvl, s));
+        } else {
+            EXACT_TRY(launch_adjoint(a, ADJ_EG_FINAL, fan, s));
+        }
         prof_end(P, u, s);
         u = prof_begin(P, 3, t, s);
-        EXACT_TRY(launch_solve_reduce(P.partials, nb, P.state, t, o.tol, o.check_every, o.stop_rule, s));
+        EXACT_TRY(launch_solve_reduce(P.partials, tvb ? P.tv_grid : nb, P.state, t, o.tol, o.check_every,
+                                      o.stop_rule, s));
         prof_end(P, u, s);
     }
     EXACT_TRY(launch_unpack(P.xr[0], P.ldr(), P.g.nx, P.g.ny, x, (o.average_tail || running) ? P.avg : nullptr,
@@ -924,7 +985,7 @@ exact_status exact_norm_estimate(exact_plan_t plan, int max_iters, double rtol, 
     const int nb_adj = adjoint_blocks(P.g.nx, P.g.ny);
     const int nb_fwd = forward_d_blocks(P.n);
     const int nb_adj_d = adjoint_d_blocks(P.g.nx, P.g.ny);
-    double *pz = P.partials + kPartStride * nb_adj;
+    double *pz = P.partials + kPartStride * (nb_adj > P.tv_grid ? nb_adj : P.tv_grid);
     double *pw = pz + nb_fwd;
     const bool fan = P.g.beam == 1;
     EXACT_TRY(launch_power_init(P.xrd, P.xcd, P.g.nx, P.g.ny, P.ldr(), P.ldc(), P.state, s));
@@ -957,7 +1018,7 @@ exact_status exact_norm_estimate_f32(exact_plan_t plan, int max_iters, double rt
     Plan &P = *reinterpret_cast<Plan *>(plan);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int nb_adj = adjoint_blocks(P.g.nx, P.g.ny);
-    double *pz = P.partials + kPartStride * nb_adj;
+    double *pz = P.partials + kPartStride * (nb_adj > P.tv_grid ? nb_adj : P.tv_grid);
     double *pw = pz + (forward_d_blocks(P.n) > kSumsqParts ? forward_d_blocks(P.n) : kSumsqParts);
     EXACT_TRY(launch_power_init_f(P.w32, P.d, P.state, s));
     FwdArgs f;
@@ -1215,7 +1276,7 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
         if (isnan(o.lo) || isnan(o.hi) || o.lo > o.hi || o.lo == INFINITY || o.hi == -INFINITY)
             return EXACT_ERR_INVALID_ARG;
         if (!isfin(o.tol) || o.tol < 0.0 || o.check_every < 0) return EXACT_ERR_INVALID_ARG;
-        if (o.average_tail || o.stop_rule != EXACT_STOP_RESIDUAL) return EXACT_ERR_UNSUPPORTED;
+        if (o.average_tail || o.stop_rule != EXACT_STOP_RESIDUAL || o.tv_bound != 0.0) return EXACT_ERR_UNSUPPORTED;
         for (int q = 0; q < j; ++q)
             if (jobs[q].plan == J.plan) return EXACT_ERR_INVALID_ARG;
         rounds = J.iters > rounds ? J.iters : rounds;

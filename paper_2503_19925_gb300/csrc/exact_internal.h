@@ -128,6 +128,10 @@ struct Plan {
     float *r = nullptr;                  // residual [n]
     double *partials = nullptr;          // per-block FP64 partial sums
     double *avg = nullptr;               // tail-average accumulator [d]
+    float *tv_step = nullptr;            // unprojected step [d] (TV-ball solves)
+    double *tv_lam = nullptr;            // [2] lam carried by the half- and full-step projections
+    void *tv_ws = nullptr;               // workspace of the TV-ball projection
+    int tv_grid = 0;                     // its cooperative grid
     double *xrd = nullptr, *xcd = nullptr;  // FP64 padded copies (power iteration)
     double *zd = nullptr;                // FP64 projections [n]
     float *w32 = nullptr;                // FP32 power-iteration image [d]
@@ -191,7 +195,10 @@ struct LinkCoef {
     float mub[kMaxBg][kMaxK];  // known-background attenuation mu_bg[m][k] log2(e)
 };
 
-enum AdjMode { ADJ_PLAIN = 0, ADJ_EG = 1, ADJ_EG_FINAL = 2 };
+// PLAIN: out = scale A^T r; EG / EG_FINAL: projected extragradient step into
+// the padded copies (FINAL adds the partial norms); STEP: out = x_base +
+// scale A^T r unprojected (the TV-ball projection follows).
+enum AdjMode { ADJ_PLAIN = 0, ADJ_EG = 1, ADJ_EG_FINAL = 2, ADJ_STEP = 3 };
 
 struct AdjArgs {
     const RayF *rays;
@@ -257,6 +264,34 @@ cudaError_t launch_power_init_f(float *w, long long d, DevState *st, cudaStream_
 cudaError_t launch_unpack(const float *xr, long long ldr, int nx, int ny, float *x, const double *avg,
                           const DevState *state, int avg_from, cudaStream_t s);
 cudaError_t launch_collapse(const void *y, int dtype, int W, long long n, float *Y, cudaStream_t s);
+// Projection onto {||x||_TV <= tau} ∩ [lo, hi]^d (k_tv.cu).  The workspace
+// (tv_workspace_bytes) holds 13 pixel arrays, FP64 partials and a TvTail.
+struct TvTail {
+    unsigned bar[2];  // grid barrier: arrivals, generation
+    int status;       // standalone calls: EXACT_OK or EXACT_ERR_TIMEOUT
+    int stats[2];     // Dykstra rounds, regularised solves of the last call
+    int pad;
+    double lam;       // standalone calls: lam in / out
+};
+struct TvLaunch {
+    int nx, ny, grid;
+    const float *z;
+    float *out, *out_r, *out_c;  // any may be null
+    long long ldr, ldc;
+    const float *old_r;          // solve path: previous iterate for the partial norms, or null
+    double *norm_part;
+    void *ws;
+    DevState *state;             // solve path: done flag and status, or null
+    double *lam_io;              // solve path: lam carried between calls, or null (tail)
+    double tau, tol_tv, tol_dykstra;
+    int fgp_iters, max_bisect, max_dykstra;
+    float lo, hi;
+};
+size_t tv_workspace_bytes(int nx, int ny, int grid);
+int tv_grid(long long d);
+TvTail *tv_tail(void *ws, int nx, int ny, int grid);
+cudaError_t launch_tv_project(const TvLaunch &L, cudaStream_t s);
+
 cudaError_t launch_solve_reduce(const double *partials, int nparts, DevState *st, int iter, double tol,
                                 int check_every, int rule, cudaStream_t s);
 cudaError_t launch_reset_state(DevState *st, cudaStream_t s);

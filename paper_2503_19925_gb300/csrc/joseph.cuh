@@ -337,6 +337,10 @@ __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, l
         const bool inside = kx < a.nx && ky < a.ny;
         if (MODE == ADJ_PLAIN) {
             if (inside) a.out[(long long)ky * a.nx + kx] = a.scale * gsum;
+        } else if (MODE == ADJ_STEP) {
+            if (inside)
+                a.out[(long long)ky * a.nx + kx] =
+                    fmaf(a.scale, gsum, ld_dyn<COHERENT>(a.base_r + (long long)ky * a.ldr + kx + kPad));
         } else {
             const long long pr = (long long)ky * a.ldr + kx + kPad;
             const float xb = inside ? ld_dyn<COHERENT>(a.base_r + pr) : 0.0f;
@@ -367,7 +371,7 @@ __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, l
             }
         }
     }
-    if (MODE == ADJ_PLAIN) return;
+    if (MODE == ADJ_PLAIN || MODE == ADJ_STEP) return;
     __syncthreads();
     // column-major copy: kTH consecutive ky per kx row
     for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {

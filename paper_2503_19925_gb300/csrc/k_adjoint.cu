@@ -165,6 +165,8 @@ cudaError_t launch_adjoint(const AdjArgs &a, int mode, bool fan, cudaStream_t s)
         return delta ? launch_adj<ADJ_PLAIN, false, true>(a, s) : launch_adj<ADJ_PLAIN, false, false>(a, s);
     }
     if (mode == ADJ_EG) return fan ? launch_adj<ADJ_EG, true, false>(a, s) : launch_adj<ADJ_EG, false, false>(a, s);
+    if (mode == ADJ_STEP)
+        return fan ? launch_adj<ADJ_STEP, true, false>(a, s) : launch_adj<ADJ_STEP, false, false>(a, s);
     return fan ? launch_adj<ADJ_EG_FINAL, true, false>(a, s) : launch_adj<ADJ_EG_FINAL, false, false>(a, s);
 }
 

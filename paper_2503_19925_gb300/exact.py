@@ -45,10 +45,22 @@ class _Windows(ctypes.Structure):
     _fields_ = [("n_windows", ctypes.c_int), ("S", ctypes.POINTER(ctypes.c_double))]
 
 
+class _TvOpts(ctypes.Structure):
+    _fields_ = [("fgp_iters", ctypes.c_int), ("max_bisect", ctypes.c_int), ("max_dykstra", ctypes.c_int),
+                ("pad", ctypes.c_int), ("tol_tv", ctypes.c_double), ("tol_dykstra", ctypes.c_double),
+                ("lam0", ctypes.c_double)]
+
+
+class _TvInfo(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int), ("solves", ctypes.c_int), ("lam", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_double), ("hi", ctypes.c_double), ("tol", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("average_tail", ctypes.c_int), ("stop_rule", ctypes.c_int),
-                ("history_cap", ctypes.c_int), ("history", ctypes.c_void_p)]
+                ("history_cap", ctypes.c_int), ("history", ctypes.c_void_p), ("tv_bound", ctypes.c_double),
+                ("tv", _TvOpts)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -90,6 +102,11 @@ _SIGS = [
     ("exact_recommended_eta", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double,
                                              ctypes.POINTER(ctypes.c_double)]),
     ("exact_plan_nnz", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    ("exact_tv_opts_default", _TvOpts, []),
+    ("exact_tv_workspace_bytes", ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+    ("exact_tv_project", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.POINTER(_TvOpts), _VP, _VP, ctypes.c_size_t,
+                                        ctypes.POINTER(_TvInfo), _VP]),
     ("exact_plan_set_background", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double), _VP]),
     ("exact_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_VP)]),
     ("exact_batch_destroy", ctypes.c_int, [_VP]),
@@ -163,6 +180,46 @@ class SolveInfo:
     rel_res: float
     status: int
     avg_change: float = 0.0
+
+
+def tv_options(changes: dict | None = None) -> _TvOpts:
+    """exact_tv_opts_default() with the given fields replaced."""
+    o = load().exact_tv_opts_default()
+    for k, v in (changes or {}).items():
+        if k not in dict(_TvOpts._fields_) or k == "pad":
+            raise KeyError(f"unknown TV option {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class TvInfo:
+    rounds: int
+    solves: int
+    lam: float
+    status: int
+
+
+def tv_project(z: torch.Tensor, tau: float, lo: float = 0.0, hi: float = math.inf, opts: dict | None = None,
+               out: torch.Tensor | None = None):
+    """Projection of the device image z [ny][nx] FP32 onto
+    {||x||_TV <= tau} ∩ [lo, hi]^d (exact_tv_project; the workspace is
+    allocated here).  Returns (x, TvInfo)."""
+    lib = load()
+    if z.dtype != torch.float32 or z.dim() != 2 or not z.is_cuda or not z.is_contiguous():
+        raise ValueError("z must be a contiguous CUDA float32 [ny][nx] tensor")
+    ny, nx = z.shape
+    nb = lib.exact_tv_workspace_bytes(nx, ny)
+    if nb == 0:
+        raise RuntimeError("exact_tv_workspace_bytes returned 0")
+    ws = torch.empty(nb, dtype=torch.uint8, device=z.device)
+    x = out if out is not None else torch.empty_like(z)
+    o = tv_options(opts)
+    info = _TvInfo()
+    _check("exact_tv_project", lib.exact_tv_project(nx, ny, _ptr(z), float(tau), float(lo), float(hi),
+                                                    ctypes.byref(o), _ptr(x), _ptr(ws), nb, ctypes.byref(info),
+                                                    _stream()))
+    return x, TvInfo(info.rounds, info.solves, info.lam, info.status)
 
 
 class Plan:
@@ -256,13 +313,16 @@ class Plan:
 
     def solve(self, y: torch.Tensor, I0: float, eta: float, iters: int, x: torch.Tensor | None = None,
               lo: float = 0.0, hi: float = math.inf, tol: float = 0.0, check_every: int = 1,
-              average_tail: bool = False, stop_rule: str = "residual", sync: bool = True):
+              average_tail: bool = False, stop_rule: str = "residual", tv_bound: float = 0.0,
+              tv_opts: dict | None = None, sync: bool = True):
         """Run up to ``iters`` extragradient iterations in place on ``x``
         (zeros if None).  stop_rule "residual" tests the relative change of the
         iterate, "average" the change of the running average of the last half
         of the iterates (and returns that average; its window ring is
-        allocated here).  Returns (x, SolveInfo); with sync=False the info is
-        filled once the current stream reaches the end of the solve."""
+        allocated here).  tv_bound > 0 intersects the box with the TV ball of
+        that radius (tv_opts: fields of exact_tv_opts to change).  Returns
+        (x, SolveInfo); with sync=False the info is filled once the current
+        stream reaches the end of the solve."""
         dt = self._y(y)
         if x is None:
             x = torch.zeros(self.shape_img, dtype=torch.float32, device=self.device)
@@ -275,7 +335,7 @@ class Plan:
             hist = torch.empty((cap,) + tuple(self.shape_img), dtype=torch.float32, device=self.device)
         opts = _SolveOpts(float(lo), float(hi), float(tol), int(check_every), int(bool(average_tail)),
                           STOP_RULES[stop_rule], 0 if hist is None else hist.shape[0],
-                          None if hist is None else hist.data_ptr())
+                          None if hist is None else hist.data_ptr(), float(tv_bound), tv_options(tv_opts))
         info = _SolveInfo()
         _check("exact_solve", load().exact_solve(self._h, _ptr(y), dt, float(I0), float(eta), int(iters),
                                                  ctypes.byref(opts), _ptr(x), ctypes.byref(info), _stream()))
@@ -414,7 +474,8 @@ class Batch:
             p._t(x, p.shape_img, name="x")
             xs.append(x)
             arr[k] = _Job(p._h.value, jb.y.data_ptr(), dt, float(jb.I0), float(jb.eta), int(jb.iters),
-                          _SolveOpts(float(jb.lo), float(jb.hi), float(jb.tol), int(jb.check_every), 0, 0, 0, None),
+                          _SolveOpts(float(jb.lo), float(jb.hi), float(jb.tol), int(jb.check_every), 0, 0, 0, None,
+                                     0.0, tv_options(None)),
                           x.data_ptr(), ctypes.pointer(infos[k]))
         _check("exact_batch_solve", load().exact_batch_solve(self._h, arr, n, _stream()))
         if torch.cuda.is_current_stream_capturing():

@@ -43,11 +43,17 @@ def test_struct_layouts_match(tmp_path):
                    'int main(void){\n'
                    'printf("%zu %zu %zu %zu\\n", sizeof(exact_geometry), offsetof(exact_geometry, pixel),'
                    ' offsetof(exact_geometry, n_bins), offsetof(exact_geometry, src_to_det));\n'
-                   'printf("%zu %zu\\n", sizeof(exact_solve_opts), offsetof(exact_solve_opts, average_tail));\n'
-                   'printf("%zu %zu\\n", sizeof(exact_solve_info), offsetof(exact_solve_info, status));\n'
+                   'printf("%zu %zu %zu %zu %zu\\n", sizeof(exact_solve_opts), offsetof(exact_solve_opts, average_tail),'
+                   ' offsetof(exact_solve_opts, history), offsetof(exact_solve_opts, tv_bound),'
+                   ' offsetof(exact_solve_opts, tv));\n'
+                   'printf("%zu %zu %zu\\n", sizeof(exact_solve_info), offsetof(exact_solve_info, status),'
+                   ' offsetof(exact_solve_info, avg_change));\n'
                    'printf("%zu %zu\\n", sizeof(exact_spectrum), sizeof(exact_windows));\n'
                    'printf("%zu %zu %zu %zu\\n", sizeof(exact_job), offsetof(exact_job, opts), offsetof(exact_job, x),'
                    ' offsetof(exact_job, info));\n'
+                   'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(exact_tv_opts), offsetof(exact_tv_opts, tol_tv),'
+                   ' offsetof(exact_tv_opts, lam0), sizeof(exact_tv_info), offsetof(exact_tv_info, lam),'
+                   ' offsetof(exact_tv_info, status));\n'
                    'return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -56,13 +62,17 @@ def test_struct_layouts_match(tmp_path):
     assert g == [ctypes.sizeof(b._Geometry), b._Geometry.pixel.offset, b._Geometry.n_bins.offset,
                  b._Geometry.src_to_det.offset]
     o = [int(v) for v in out[1].split()]
-    assert o == [ctypes.sizeof(b._SolveOpts), b._SolveOpts.average_tail.offset]
+    assert o == [ctypes.sizeof(b._SolveOpts), b._SolveOpts.average_tail.offset, b._SolveOpts.history.offset,
+                 b._SolveOpts.tv_bound.offset, b._SolveOpts.tv.offset]
     i = [int(v) for v in out[2].split()]
-    assert i == [ctypes.sizeof(b._SolveInfo), b._SolveInfo.status.offset]
+    assert i == [ctypes.sizeof(b._SolveInfo), b._SolveInfo.status.offset, b._SolveInfo.avg_change.offset]
     s = [int(v) for v in out[3].split()]
     assert s == [ctypes.sizeof(b._Spectrum), ctypes.sizeof(b._Windows)]
     jv = [int(v) for v in out[4].split()]
     assert jv == [ctypes.sizeof(b._Job), b._Job.opts.offset, b._Job.x.offset, b._Job.info.offset]
+    tv = [int(v) for v in out[5].split()]
+    assert tv == [ctypes.sizeof(b._TvOpts), b._TvOpts.tol_tv.offset, b._TvOpts.lam0.offset,
+                  ctypes.sizeof(b._TvInfo), b._TvInfo.lam.offset, b._TvInfo.status.offset]
 
 
 def test_product_path_never_imports_the_oracle():
