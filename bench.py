@@ -56,6 +56,7 @@ def parse_args(argv=None):
     p.add_argument("--batch-jobs", type=int, default=64)
     p.add_argument("--batch-iters", type=int, default=None)
     p.add_argument("--no-served", action="store_true", help="skip the serving measurement")
+    p.add_argument("--no-tv", action="store_true", help="skip the TV-ball feasible-set measurement")
     p.add_argument("--serve-jobs", type=int, default=32)
     p.add_argument("--serve-loads", default="0.8,1.5",
                    help="arrival rates as fractions of the measured sequential capacity")
@@ -320,6 +321,104 @@ def make_job_inputs(ex, torch, spec, dev, rank=0):
     return plan, y, eta, xs
 
 
+def tv_norm_np(x) -> float:
+    """Isotropic TV (forward differences, zero past the last row/column) of a
+    host image: the radius of the TV ball, set to the target's TV as in
+    Sec. 3.1 (a workload parameter)."""
+    x = np.asarray(x, dtype=np.float64)
+    gx = np.zeros_like(x)
+    gy = np.zeros_like(x)
+    gx[:, :-1] = x[:, 1:] - x[:, :-1]
+    gy[:-1, :] = x[1:, :] - x[:-1, :]
+    return float(np.sqrt(gx * gx + gy * gy).sum())
+
+
+def run_tv(ex, torch, dev, rank: int):
+    """The feasible set of the experiments of Sec. 3.1, X = TV ball ∩ orthant
+    (radius = the target's TV): (a) one projection of a noisy 512^2 phantom;
+    (b) extragradient iterations on X at the 512^2 fan workload; (c) the
+    Sec. 3.1-sized problem (25^2 image, 50 views x 50 bins fan, 3 windows over
+    50 energies, I0 = 1e6) solved to the paper's stopping rule
+    ||xbar_t - xbar_{t-1}|| <= 1e-5 on the running average."""
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    cfg, S, mu, xs, seed = workload("C3")
+    tau = tv_norm_np(xs)
+    noisy = xs + 0.15 * np.random.default_rng(seed + 3).normal(size=xs.shape)
+    z = torch.tensor(noisy, dtype=torch.float32, device=dev)
+    # the paper's tolerances (0.01 on the TV, 1e-4 on ||z_{k+1} - z_k||) are
+    # for a 25^2 image; here the TV one is relative to tau and the Dykstra one
+    # scaled by sqrt(pixels / 625)
+    d = xs.size
+    opts = {"tol_tv": 1e-3 * tau, "tol_dykstra": 1e-4 * math.sqrt(d / 625.0)}
+    ex.tv_project(z, tau, opts=opts)  # warm
+    times, info = [], None
+    for _ in range(3):
+        a = ev()
+        _, info = ex.tv_project(z, tau, opts=opts)
+        b = ev()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    fgp = ex.tv_options(opts).fgp_iters
+    ms = statistics.median(times)
+    out["projection_512"] = {"ms": ms, "dykstra_rounds": info.rounds, "regularised_solves": info.solves,
+                             "dual_steps_per_s": info.solves * fgp / (ms / 1e3), "tau": tau,
+                             "options": {"fgp_iters": fgp, **opts}}
+    # (b) extragradient iterations on X at the 512^2 fan workload
+    plan = ex.Plan(ex.Geometry(**cfg["geometry"]), mu, S)
+    zt = plan.forward(torch.tensor(xs, dtype=torch.float32, device=dev)).double()
+    lam = cfg["I0"] * torch.einsum("wk,kvb->wvb", torch.tensor(S, dtype=torch.float64, device=dev),
+                                   torch.exp(-torch.tensor(mu, dtype=torch.float64, device=dev)[:, None, None]
+                                             * zt.clamp_min(0)[None]))
+    gen = torch.Generator(device=dev).manual_seed(seed + 1 + 7919 * rank)
+    y = torch.poisson(lam, generator=gen).to(torch.bfloat16).contiguous()
+    normA, _ = plan.norm_estimate(max_iters=100, rtol=1e-6)
+    eta = plan.recommended_eta(cfg["I0"], normA)
+    # start near the box-constrained solution, where the TV constraint is active
+    x0, _ = plan.solve(y, cfg["I0"], eta, 200)
+    iters = 3
+    x = x0.clone()
+    plan.solve(y, cfg["I0"], eta, 1, x=x, tv_bound=tau, tv_opts=opts)
+    x = x0.clone()
+    a = ev()
+    x, sinfo = plan.solve(y, cfg["I0"], eta, iters, x=x, tv_bound=tau, tv_opts=opts)
+    b = ev()
+    b.synchronize()
+    out["solve_512_fan"] = {"iters": iters, "ms_per_iter": a.elapsed_time(b) / iters, "status": sinfo.status,
+                            "start": "x after 200 box-constrained iterations (TV above tau)",
+                            "tv_start": tv_norm_np(x0.cpu().numpy())}
+    plan.close()
+    # (c) the Sec. 3.1-sized problem to the paper's stopping rule
+    geom = dict(beam=1, nx=25, ny=25, n_views=50, n_bins=50, angle_range=2 * math.pi, bin_pitch=1.5,
+                src_to_center=40.0, src_to_det=60.0)
+    spec = dict(geometry=geom, K=50, W=3, I0=1e6, seed=synth.case_seed("Sec3.1"))
+    plan, y, mu3, S3, xs3 = make_counts(ex, torch, spec, dev, rank)
+    normA, _ = plan.norm_estimate(max_iters=200, rtol=1e-9)
+    eta = plan.recommended_eta(spec["I0"], normA)
+    tau3 = tv_norm_np(xs3)
+    max_iters = 3000
+    a = ev()
+    x, sinfo = plan.solve(y, spec["I0"], eta, max_iters, tv_bound=tau3, stop_rule="average", tol=1e-5)
+    b = ev()
+    b.synchronize()
+    xg = x.double().cpu().numpy()
+    rmse = float(np.sqrt(((xg - xs3) ** 2).mean()))
+    out["paper_sec3_1"] = {"workload": "25^2 random-ellipse phantom, fan 50 views x 50 bins over 360 deg, 3 windows "
+                                       "over 50 energies, I0 = 1e6, Poisson; X = TV ball (target TV) ∩ orthant; "
+                                       "stop ||xbar_t - xbar_{t-1}|| <= 1e-5",
+                           "iters": sinfo.iters_done, "ms": a.elapsed_time(b), "avg_change": sinfo.avg_change,
+                           "rmse": rmse, "psnr_db": 20.0 * math.log10(max(xs3.max(), 1e-12) / max(rmse, 1e-30)),
+                           "status": sinfo.status}
+    plan.close()
+    return out
+
+
 def run_batched(ex, torch, dev, n_jobs: int, iters: int, rank: int):
     """The batched mix: n_jobs reconstructions of uneven size/views/windows,
     (a) one after another with exact_solve, (b) in one persistent launch with
@@ -551,6 +650,8 @@ def run_exact(args):
     if not args.no_served:
         line["served"] = run_served(ex, torch, dev, args.serve_jobs,
                                     [float(v) for v in args.serve_loads.split(",") if v], rank)
+    if not args.no_tv:
+        line["tv"] = run_tv(ex, torch, dev, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_baseline_iters)
     if rank == 0:

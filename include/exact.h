@@ -190,8 +190,8 @@ typedef enum {
  * disables the lower bound); tv_bound > 0 intersects it with the TV ball of
  * Sec. 3.1 (each half and full step then projects with exact_tv_project's
  * algorithm, the bisection of each of the two projections starting from its
- * lam of the previous iteration; only stop_rule EXACT_STOP_RESIDUAL without
- * average_tail, else EXACT_ERR_UNSUPPORTED).  Iterations are counted
+ * lam of the previous iteration; average_tail must be 0, else
+ * EXACT_ERR_UNSUPPORTED).  Iterations are counted
  * t = 1, 2, ...; x_t is the iterate after t of them.
  *  - stop_rule EXACT_STOP_RESIDUAL: if tol > 0 and check_every > 0 the solve
  *    stops after the first t that is a multiple of check_every with

@@ -159,26 +159,33 @@ def project_tv_box(z, tau: float, lo: float = 0.0, hi: float = np.inf, opts: TvO
 
 @dataclass
 class TvSolveResult:
-    x: np.ndarray
+    x: np.ndarray            # x_T, or xbar_T with the running-average rule
     rel_res: np.ndarray
     lam_half: float
     lam_full: float
+    iters: int = 0
+    changes: np.ndarray | None = None  # running-average rule: ||xbar_t - xbar_{t-1}||, t = 2 .. T
 
 
 def solve_tv(g, S, mu, I0: float, y, eta: float, iters: int, tau: float, lo: float = 0.0, hi: float = np.inf,
-             opts: TvOptions | None = None, x1=None, bg=None) -> TvSolveResult:
+             opts: TvOptions | None = None, x1=None, bg=None, running_average: bool = False, tol: float = 0.0,
+             check_every: int = 1) -> TvSolveResult:
     """Projected extragradient (Eq. (11)) on X = {||x||_TV <= tau} ∩ [lo, hi]^d:
         x_{t+1/2} = P_X(x_t - eta F(x_t)),  x_{t+1} = P_X(x_t - eta F(x_{t+1/2})),
     P_X by project_tv_box.  Each of the two projections of an iteration starts
     its bisection from its own lam of the previous iteration (opts.lam0 at the
-    first).  x1 (default 0) is clamped to the box only (0 lies in X)."""
+    first).  x1 (default 0) is clamped to the box only (0 lies in X).  With
+    running_average the stopping rule and output of Sec. 3.1 apply (see
+    oracle.solve_running_average), else the relative-change rule with tol."""
     import oracle
     opts = opts or TvOptions()
     x = np.zeros((g.ny, g.nx)) if x1 is None else np.array(x1, dtype=np.float64).reshape(g.ny, g.nx)
     x = np.clip(x, lo, hi)
     lam_h = lam_f = opts.lam0
-    rel = []
-    for _ in range(iters):
+    rel, window, changes = [], [], []
+    prev = None
+    t = 0
+    for t in range(1, iters + 1):
         w = x - eta * oracle.operator(g, x, S, mu, I0, y, bg)
         r1 = project_tv_box(w, tau, lo, hi, TvOptions(**{**opts.__dict__, "lam0": lam_h}))
         lam_h = r1.lam
@@ -187,4 +194,19 @@ def solve_tv(g, S, mu, I0: float, y, eta: float, iters: int, tau: float, lo: flo
         lam_f = r2.lam
         rel.append(float(np.linalg.norm(r2.x - x) / max(np.linalg.norm(x), 1e-30)))
         x = r2.x
-    return TvSolveResult(x, np.array(rel), lam_h, lam_f)
+        stop = False
+        if running_average:
+            window.append(x.copy())
+            m = oracle.window_size(t)
+            del window[:-m]
+            xbar = sum(window) / m
+            if prev is not None:
+                changes.append(float(np.linalg.norm(xbar - prev)))
+                stop = tol > 0.0 and check_every > 0 and t % check_every == 0 and changes[-1] <= tol
+            prev = xbar
+        else:
+            stop = tol > 0.0 and check_every > 0 and t % check_every == 0 and rel[-1] <= tol
+        if stop:
+            break
+    out = (sum(window) / len(window)) if running_average and window else x
+    return TvSolveResult(out, np.array(rel), lam_h, lam_f, t, np.array(changes) if running_average else None)

@@ -827,7 +827,7 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     if (tvb && (o.tv.fgp_iters < 1 || o.tv.max_bisect < 1 || o.tv.max_dykstra < 0 || !(o.tv.tol_tv >= 0.0) ||
                 !(o.tv.tol_dykstra >= 0.0) || isnan(o.tv.lam0) || o.tv.lam0 == INFINITY))
         return EXACT_ERR_INVALID_ARG;
-    if (tvb && (running || o.average_tail)) return EXACT_ERR_UNSUPPORTED;
+    if (tvb && o.average_tail) return EXACT_ERR_UNSUPPORTED;
     Plan &P = *reinterpret_cast<Plan *>(plan);
     if (tvb && !P.tv_ws) return EXACT_ERR_CUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -922,6 +922,7 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
             tvl.out_r = P.xr[1];
             tvl.out_c = P.xc[1];
             tvl.old_r = nullptr;
+            tvl.hist = nullptr;
             tvl.lam_io = P.tv_lam;
             EXACT_TRY(launch_tv_project(tvl, s));
         } else {
@@ -955,6 +956,12 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
             tvl.old_r = P.xr[0];
             tvl.norm_part = P.partials;
             tvl.lam_io = P.tv_lam + 1;
+            tvl.avg = a.avg;
+            tvl.hist = a.hist;
+            tvl.hist_put = a.hist_put;
+            tvl.hist_drop = a.hist_drop;
+            tvl.inv_m = a.inv_m;
+            tvl.inv_m_prev = a.inv_m_prev;
             EXACT_TRY(launch_tv_project(tvl, s));
         } else {
             EXACT_TRY(launch_adjoint(a, ADJ_EG_FINAL, fan, s));

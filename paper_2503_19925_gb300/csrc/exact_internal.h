@@ -280,6 +280,11 @@ struct TvLaunch {
     long long ldr, ldc;
     const float *old_r;          // solve path: previous iterate for the partial norms, or null
     double *norm_part;
+    // solve path, running-average rule (see AdjArgs; null hist: off)
+    double *avg;
+    float *hist;
+    int hist_put, hist_drop;
+    double inv_m, inv_m_prev;
     void *ws;
     DevState *state;             // solve path: done flag and status, or null
     double *lam_io;              // solve path: lam carried between calls, or null (tail)

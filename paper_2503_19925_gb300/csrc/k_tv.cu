@@ -42,6 +42,10 @@ struct TvArgs {
     long long ldr, ldc;
     const float *old_r;    // padded row-major previous iterate: partial norms of the solve, or null
     double *norm_part;     // [kPartStride * grid] when old_r is set
+    double *avg;           // running-average rule: FP64 window sum (null hist: off)
+    float *hist;
+    int hist_put, hist_drop;
+    double inv_m, inv_m_prev;
     float *zk, *pk, *qk, *w, *xt;
     float *dual[8];        // px, py, rx, ry and their second buffers
     double *part;          // [2][grid] FP64 partial sums
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_project(TvArgs a)
         if (sqrt(chg) <= a.tol_dyk) break;
     }
     // result, padded copies and (solve path) the partial norms of the step
-    double s0 = 0.0, s1 = 0.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (long long q = first; q < a.d; q += stride) {
         const float v = __ldcg(a.zk + q);
         const int i = (int)(q / nx), j = (int)(q - (long long)i * nx);
@@ -260,17 +264,26 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_project(TvArgs a)
             const double dd = (double)v - xb;
             s0 += dd * dd;
             s1 += xb * xb;
+            if (a.hist) {  // running average of Sec. 3.1, as in the extragradient epilogue
+                const double sp = a.avg[q];
+                double sn = sp + (double)v;
+                if (a.hist_drop >= 0) sn -= (double)a.hist[(long long)a.hist_drop * a.d + q];
+                a.hist[(long long)a.hist_put * a.d + q] = v;
+                a.avg[q] = sn;
+                const double dv = sn * a.inv_m - sp * a.inv_m_prev;
+                s2 += dv * dv;
+            }
         }
         if (a.out) a.out[q] = v;
         if (a.out_r) a.out_r[(long long)i * a.ldr + j + kPad] = v;
         if (a.out_c) a.out_c[(long long)j * a.ldc + i + kPad] = v;
     }
     if (a.old_r) {
-        const double b0 = block_sum(s0), b1 = block_sum(s1);
+        const double b0 = block_sum(s0), b1 = block_sum(s1), b2 = block_sum(s2);
         if (threadIdx.x == 0) {
             a.norm_part[kPartStride * blockIdx.x] = b0;
             a.norm_part[kPartStride * blockIdx.x + 1] = b1;
-            a.norm_part[kPartStride * blockIdx.x + 2] = 0.0;
+            a.norm_part[kPartStride * blockIdx.x + 2] = b2;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -330,6 +343,12 @@ cudaError_t launch_tv_project(const TvLaunch &L, cudaStream_t s)
     a.ldc = L.ldc;
     a.old_r = L.old_r;
     a.norm_part = L.norm_part;
+    a.avg = L.avg;
+    a.hist = L.hist;
+    a.hist_put = L.hist_put;
+    a.hist_drop = L.hist_drop;
+    a.inv_m = L.inv_m;
+    a.inv_m_prev = L.inv_m_prev;
     // workspace layout: 13 pixel arrays, partial sums, tail words
     char *p = static_cast<char *>(L.ws);
     const size_t fb = tv_align(sizeof(float) * (size_t)a.d);

@@ -90,3 +90,29 @@ def test_tv_options_rejected():
         ex.tv_project(z, -1.0)
     with pytest.raises(RuntimeError):
         ex.tv_project(z, 1.0, opts=dict(fgp_iters=0))
+
+
+def test_solve_on_tv_ball_with_the_running_average_rule():
+    geom = dict(beam=1, nx=40, ny=36, n_views=30, n_bins=61, angle_range=2 * math.pi, bin_pitch=1.5,
+                src_to_center=150.0, src_to_det=240.0)
+    p = problem(geom, K=6, W=2, I0=1e4, seed=8)
+    nA, _ = oracle.norm_estimate(p["g_or"], 300, 1e-10)
+    eta = 1.0 / (4.0 * oracle.lipschitz(nA, p["S"], p["mu"], p["I0"], p["S"].shape[0] * p["g_or"].n_rays))
+    tau = T.tv(p["xs"])
+    o = dict(fgp_iters=20, max_bisect=30, max_dykstra=10, tol_tv=1e-4 * tau, tol_dykstra=1e-3)
+    iters = 24
+    full = T.solve_tv(p["g_or"], p["S"], p["mu"], p["I0"], p["y"], eta, iters, tau, opts=T.TvOptions(**o),
+                      running_average=True)
+    ch = full.changes
+    tol = math.sqrt(ch[12] * ch[13])
+    expect = next(t for t in range(2, iters + 1) if ch[t - 2] <= tol)
+    ref = T.solve_tv(p["g_or"], p["S"], p["mu"], p["I0"], p["y"], eta, iters, tau, opts=T.TvOptions(**o),
+                     running_average=True, tol=tol)
+    assert ref.iters == expect
+    plan = ex.Plan(ex.Geometry(**geom), p["mu"], p["S"])
+    y = torch.as_tensor(p["y"], dtype=torch.float32, device=DEV)
+    x, info = plan.solve(y, p["I0"], eta, iters, tv_bound=tau, tv_opts=o, stop_rule="average", tol=tol)
+    assert info.status == 0 and info.iters_done == expect
+    xg = x.double().cpu().numpy()
+    assert rel_l2(xg, ref.x) <= 1e-3
+    assert info.avg_change == pytest.approx(ch[expect - 2], rel=1e-2)
