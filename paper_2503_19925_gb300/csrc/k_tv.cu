@@ -155,9 +155,78 @@ __device__ __forceinline__ float prox_x(const float *w, const float *rx, const f
     return fmaf(theta, dv, __ldcg(w + q));
 }
 
+// One dual step of the fast gradient projection method over the image, tile
+// by tile: a kTvTH x kTvTW tile with its one-pixel halo of w, rx, ry is staged
+// in shared memory (coalesced), x = w + theta div r is formed on the tile and
+// one extra row and column, and each pixel updates (p, r) from grad x.
+constexpr int kTvTW = 32, kTvTH = kTvThreads / kTvTW;
+
+struct TvSmem {
+    float w[kTvTH + 2][kTvTW + 2], rx[kTvTH + 2][kTvTW + 2], ry[kTvTH + 2][kTvTW + 2];
+    float x[kTvTH + 1][kTvTW + 1];
+};
+
+__device__ void fgp_step(const TvArgs &a, TvSmem &sm, const float *rx, const float *ry, const float *px,
+                         const float *py, float *px2, float *py2, float *rx2, float *ry2, float theta, float step,
+                         float beta)
+{
+    const int nx = a.nx, ny = a.ny;
+    const int tiles_x = (nx + kTvTW - 1) / kTvTW, tiles = tiles_x * ((ny + kTvTH - 1) / kTvTH);
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int i0 = (tile / tiles_x) * kTvTH, j0 = (tile % tiles_x) * kTvTW;
+        // stage rows i0-1 .. i0+TH, columns j0-1 .. j0+TW (zeros outside the image)
+        for (int e = threadIdx.x; e < (kTvTH + 2) * (kTvTW + 2); e += kTvThreads) {
+            const int li = e / (kTvTW + 2), lj = e % (kTvTW + 2);
+            const int gi = i0 - 1 + li, gj = j0 - 1 + lj;
+            float vw = 0.0f, vx = 0.0f, vy = 0.0f;
+            if (gi >= 0 && gi < ny && gj >= 0 && gj < nx) {
+                const long long q = (long long)gi * nx + gj;
+                vw = __ldcg(a.w + q);
+                vx = __ldcg(rx + q);
+                vy = __ldcg(ry + q);
+            }
+            sm.w[li][lj] = vw;
+            sm.rx[li][lj] = vx;
+            sm.ry[li][lj] = vy;
+        }
+        __syncthreads();
+        // x on tile rows 0 .. TH and columns 0 .. TW (the extra row / column
+        // feed the forward differences of the last ones)
+        for (int e = threadIdx.x; e < (kTvTH + 1) * (kTvTW + 1); e += kTvThreads) {
+            const int li = e / (kTvTW + 1), lj = e % (kTvTW + 1);
+            const int gi = i0 + li, gj = j0 + lj;
+            float dv = 0.0f;
+            if (gj < nx - 1) dv += sm.rx[li + 1][lj + 1];
+            if (gj > 0) dv -= sm.rx[li + 1][lj];
+            if (gi < ny - 1) dv += sm.ry[li + 1][lj + 1];
+            if (gi > 0) dv -= sm.ry[li][lj + 1];
+            sm.x[li][lj] = fmaf(theta, dv, sm.w[li + 1][lj + 1]);
+        }
+        __syncthreads();
+        const int li = threadIdx.x / kTvTW, lj = threadIdx.x % kTvTW;
+        const int gi = i0 + li, gj = j0 + lj;
+        if (gi < ny && gj < nx) {
+            const long long q = (long long)gi * nx + gj;
+            const float x0 = sm.x[li][lj];
+            const float gx = gj < nx - 1 ? sm.x[li][lj + 1] - x0 : 0.0f;
+            const float gy = gi < ny - 1 ? sm.x[li + 1][lj] - x0 : 0.0f;
+            const float qx = fmaf(step, gx, sm.rx[li + 1][lj + 1]);
+            const float qy = fmaf(step, gy, sm.ry[li + 1][lj + 1]);
+            const float nrm = fmaxf(1.0f, sqrtf(qx * qx + qy * qy));
+            const float nx_ = qx / nrm, ny_ = qy / nrm;
+            px2[q] = nx_;
+            py2[q] = ny_;
+            rx2[q] = fmaf(beta, nx_ - __ldcg(px + q), nx_);
+            ry2[q] = fmaf(beta, ny_ - __ldcg(py + q), ny_);
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kTvThreads) k_tv_project(TvArgs a)
 {
     if (a.done && ld_volatile_i32(a.done)) return;
+    __shared__ TvSmem sm;
     const long long stride = (long long)gridDim.x * kTvThreads;
     const long long first = (long long)blockIdx.x * kTvThreads + threadIdx.x;
     const int nx = a.nx, ny = a.ny;
@@ -198,20 +267,7 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_project(TvArgs a)
                 for (int it = 0; it < a.fgp_iters; ++it) {
                     const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
                     const float beta = (float)((t - 1.0) / tn);
-                    for (long long q = first; q < a.d; q += stride) {
-                        const int i = (int)(q / nx), j = (int)(q - (long long)i * nx);
-                        const float x0 = prox_x(a.w, rx, ry, theta, i, j, nx, ny);
-                        const float gx = j < nx - 1 ? prox_x(a.w, rx, ry, theta, i, j + 1, nx, ny) - x0 : 0.0f;
-                        const float gy = i < ny - 1 ? prox_x(a.w, rx, ry, theta, i + 1, j, nx, ny) - x0 : 0.0f;
-                        const float qx = fmaf(step, gx, __ldcg(rx + q));
-                        const float qy = fmaf(step, gy, __ldcg(ry + q));
-                        const float nrm = fmaxf(1.0f, sqrtf(qx * qx + qy * qy));
-                        const float nx_ = qx / nrm, ny_ = qy / nrm;
-                        px2[q] = nx_;
-                        py2[q] = ny_;
-                        rx2[q] = fmaf(beta, nx_ - __ldcg(px + q), nx_);
-                        ry2[q] = fmaf(beta, ny_ - __ldcg(py + q), ny_);
-                    }
+                    fgp_step(a, sm, rx, ry, px, py, px2, py2, rx2, ry2, theta, step, beta);
                     if (!grid_barrier(a.bar, a.err, a.done)) return;
                     float *tp;
                     tp = px; px = px2; px2 = tp;
@@ -315,7 +371,7 @@ int tv_grid(long long d)
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tv_project, kTvThreads, 0) != cudaSuccess)
             return 0;
         if (per < 1) return 0;
-        g_tv_grid[dev] = sms * (per < 2 ? per : 2);
+        g_tv_grid[dev] = sms * (per < 4 ? per : 4);
     }
     const long long need = (d + kTvThreads - 1) / kTvThreads;
     return (int)(need < g_tv_grid[dev] ? (need > 0 ? need : 1) : g_tv_grid[dev]);
