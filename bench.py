@@ -316,6 +316,7 @@ def run_served(ex, torch, dev, n_jobs: int, loads, rank: int):
 def make_job_inputs(ex, torch, spec, dev, rank=0):
     """Plan, counts, step size and ground truth of one synthetic job."""
     plan, y, mu, S, xs = make_counts(ex, torch, spec, dev, rank)
+    plan.autotune()
     normA, _ = plan.norm_estimate(max_iters=100, rtol=1e-6)
     eta = plan.recommended_eta(spec["I0"], normA)
     return plan, y, eta, xs
@@ -445,6 +446,8 @@ def run_batched(ex, torch, dev, n_jobs: int, iters: int, rank: int):
     bjobs = [ex.Job(plan=p, y=y, I0=sp["I0"], eta=eta, iters=iters, x=x)
              for (p, y, eta, _), x, sp in zip(jobs_in, xs_b, specs)]
 
+    policy = batch.autotune(bjobs)
+
     def batch_pass():
         for x in xs_b:
             x.zero_()
@@ -499,7 +502,9 @@ def run_batched(ex, torch, dev, n_jobs: int, iters: int, rank: int):
         "batched": {"recon_per_s": n_jobs / (b_ms / 1e3), "ms": b_ms, "p50_latency_ms": b_ms, "p99_latency_ms": b_ms,
                     "mean_psnr_db": psnr_b},
         "batched_graph": {"recon_per_s": n_jobs / (g_ms / 1e3), "ms": g_ms, "mean_psnr_db": psnr_g},
-        "speedup_vs_sequential": seq_ms / b_ms}
+        "speedup_vs_sequential": seq_ms / b_ms,
+        "tuning": {"batch_split_policy": ["one CTA per tile", "per-plan adj_split"][policy],
+                   "plan_adj_splits": sorted({p.tuning["adj_split"] for p, _, _, _ in jobs_in})}}
     batch.close()
     for p, _, _, _ in jobs_in:
         p.close()
@@ -524,6 +529,9 @@ def run_exact(args):
     t0 = time.perf_counter()
     plan = ex.Plan(geom, mu, S)
     plan_ms = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    tuning = plan.autotune()
+    tune_ms = 1e3 * (time.perf_counter() - t0)
     t0 = time.perf_counter()
     normA, norm_iters = plan.norm_estimate(max_iters=500, rtol=1e-9)
     norm_ms = 1e3 * (time.perf_counter() - t0)
@@ -644,7 +652,7 @@ def run_exact(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks.summary(),
             "psnr_db": psnr, "eta": eta, "normA_sq": normA, "norm_estimate": {"ms": norm_ms, "iters": norm_iters},
-            "plan_create_ms": plan_ms}
+            "plan_create_ms": plan_ms, "tuning": {**tuning, "autotune_ms": tune_ms}}
     if not args.no_batched:
         line["batched"] = run_batched(ex, torch, dev, args.batch_jobs, args.batch_iters or configs.C4["iters"], rank)
     if not args.no_served:

@@ -179,6 +179,29 @@ exact_status exact_tv_project(int nx, int ny, const float *z, double tau, double
                               const exact_tv_opts *opts, float *x, void *workspace, size_t workspace_bytes,
                               exact_tv_info *info, exact_stream_t stream);
 
+/* Kernel tuning of a plan (no counterpart in the paper: a property of this
+ * implementation).  adj_split: CTAs sharing one 16 x 16-pixel tile of the
+ * adjoint, each taking an interleaved subset of the views (1..8); the tile's
+ * partial sums are added in split order, so results are deterministic for a
+ * given value and differ only in FP32 rounding between values.  Small images
+ * want larger splits (more CTAs than tiles).  reserved must be zero. */
+typedef struct {
+    int adj_split;
+    int reserved[7];
+} exact_tuning;
+
+exact_status exact_plan_get_tuning(exact_plan_t plan, exact_tuning *out);
+exact_status exact_plan_set_tuning(exact_plan_t plan, const exact_tuning *tuning);
+
+/* Autotuner: times the adjoint of this plan's geometry on the device for
+ * adj_split in {1, 2, 3, 4, 6, 8} (median of 5 launches each) and keeps the
+ * fastest, a larger split only when it is more than 3% faster.  The choice is
+ * cached per geometry shape (beam, nx, ny, n_views, n_bins) for the life of
+ * the process: later plans of a tuned shape take it without timing unless
+ * force != 0.  out may be NULL.  Uses the plan's workspace as scratch;
+ * synchronises the stream. */
+exact_status exact_plan_autotune(exact_plan_t plan, int force, exact_tuning *out, exact_stream_t stream);
+
 /* Stopping rules of exact_solve (see exact_solve_opts). */
 typedef enum {
     EXACT_STOP_RESIDUAL = 0, /* relative change of the iterate */
@@ -341,6 +364,17 @@ exact_status exact_batch_destroy(exact_batch_t batch);
  * The context's staging is reused by the next call, which waits for this call's
  * staging copy first. */
 exact_status exact_batch_solve(exact_batch_t batch, const exact_job *jobs, int n_jobs, exact_stream_t stream);
+
+/* Autotuner of a batch context (no counterpart in the paper): times
+ * exact_batch_solve on these jobs, two iterations each (best of two after a
+ * warm-up run), under each adjoint split policy -- 0: one CTA per adjoint
+ * tile; 1: each plan's own exact_tuning.adj_split -- and keeps the faster one
+ * (policy 1 only when more than 3% faster) for later exact_batch_solve calls
+ * of this context.  Every job's x is saved in its plan's workspace and
+ * restored after each trial, and the jobs' info structs are not written.
+ * policy_out may be NULL.  Synchronises. */
+exact_status exact_batch_autotune(exact_batch_t batch, const exact_job *jobs, int n_jobs, int *policy_out,
+                                  exact_stream_t stream);
 
 /* Number of nonzero entries of A (pairs of ray and pixel with a positive
  * Joseph weight), counted in FP64 on the host at plan creation: the

@@ -3,6 +3,10 @@
 // that enqueue the kernels of k_forward.cu, k_adjoint.cu and k_util.cu.
 #include "exact_internal.h"
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+
 #include <climits>
 #include <cudaTypedefs.h>
 #include <math.h>
@@ -369,6 +373,8 @@ size_t carve(Plan &P, char *base)
     P.zd = c.take<double>(base, (size_t)P.n);
     P.w32 = c.take<float>(base, (size_t)P.d);
     P.state = c.take<DevState>(base, 1);
+    P.split_part = c.take<float>(base, (size_t)nb_adj * kMaxSplit * kTH * kTW);
+    P.split_count = c.take<int>(base, (size_t)nb_adj);
     P.tv_step = c.take<float>(base, (size_t)P.d);
     P.tv_lam = c.take<double>(base, 2);
     if (P.tv_grid > 0) P.tv_ws = c.take<char>(base, tv_workspace_bytes(nx, ny, P.tv_grid));
@@ -710,9 +716,122 @@ exact_status exact_plan_bind_workspace(exact_plan_t plan, void *dev_ptr, size_t 
             return EXACT_ERR_CUDA;
         }
     }
+    if (cudaMemset(P->split_count, 0, sizeof(int) * (size_t)adjoint_blocks(P->g.nx, P->g.ny)) != cudaSuccess) {
+        P->ws = nullptr;
+        P->ws_bytes = 0;
+        return EXACT_ERR_CUDA;
+    }
     P->ws = dev_ptr;
     P->ws_bytes = bytes;
     return EXACT_OK;
+}
+
+// ---------------------------------------------------------------- tuning
+
+namespace {
+
+constexpr int kSplitCandidates[] = {1, 2, 3, 4, 6, 8};
+
+struct TuneKey {
+    int beam, nx, ny, views, bins;
+    bool operator<(const TuneKey &o) const
+    {
+        if (beam != o.beam) return beam < o.beam;
+        if (nx != o.nx) return nx < o.nx;
+        if (ny != o.ny) return ny < o.ny;
+        if (views != o.views) return views < o.views;
+        return bins < o.bins;
+    }
+};
+
+std::mutex g_tune_lock;
+std::map<TuneKey, int> g_tune_cache;  // adj_split chosen per geometry shape, this process
+
+}  // namespace
+
+exact_status exact_plan_get_tuning(exact_plan_t plan, exact_tuning *out)
+{
+    if (!plan || !out) return EXACT_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    out->adj_split = reinterpret_cast<Plan *>(plan)->adj_split;
+    return EXACT_OK;
+}
+
+exact_status exact_plan_set_tuning(exact_plan_t plan, const exact_tuning *t)
+{
+    if (!plan || !t || t->adj_split < 1 || t->adj_split > kMaxSplit) return EXACT_ERR_INVALID_ARG;
+    reinterpret_cast<Plan *>(plan)->adj_split = t->adj_split;
+    return EXACT_OK;
+}
+
+exact_status exact_plan_autotune(exact_plan_t plan, int force, exact_tuning *out, exact_stream_t stream)
+{
+    exact_status st = check_plan(plan, true);
+    if (st != EXACT_OK) return st;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    const TuneKey key{P.g.beam, P.g.nx, P.g.ny, P.g.n_views, P.g.n_bins};
+    if (!force) {
+        std::lock_guard<std::mutex> guard(g_tune_lock);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            P.adj_split = it->second;
+            return out ? exact_plan_get_tuning(plan, out) : EXACT_OK;
+        }
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    EXACT_TRY(cudaMemsetAsync(P.r, 0, sizeof(float) * (size_t)P.n, s));
+    AdjArgs a;
+    memset(&a, 0, sizeof(a));
+    a.rays = P.rays_f;
+    a.walk = P.rays_w;
+    a.views = P.views;
+    a.n_views = P.g.n_views;
+    a.n_bins = P.g.n_bins;
+    a.nx = P.g.nx;
+    a.ny = P.g.ny;
+    a.r = P.r;
+    a.scale = 1.0f;
+    a.out = P.w32;
+    a.split_part = P.split_part;
+    a.split_count = P.split_count;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return EXACT_ERR_CUDA;
+    }
+    const bool fan = P.g.beam == 1;
+    int best = 1;
+    float best_ms = INFINITY;
+    cudaError_t e = cudaSuccess;
+    for (int cand : kSplitCandidates) {
+        a.nsplit = cand;
+        constexpr int kReps = 5;
+        float ms[kReps];
+        e = launch_adjoint(a, ADJ_PLAIN, fan, s);  // warm
+        for (int r = 0; r < kReps && e == cudaSuccess; ++r) {
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = launch_adjoint(a, ADJ_PLAIN, fan, s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[r], e0, e1);
+        }
+        if (e != cudaSuccess) break;
+        std::sort(ms, ms + kReps);
+        // prefer fewer CTAs per tile unless a larger split is clearly faster
+        if (ms[kReps / 2] < 0.97f * best_ms) {
+            best_ms = ms[kReps / 2];
+            best = cand;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_status(e);
+    P.adj_split = best;
+    {
+        std::lock_guard<std::mutex> guard(g_tune_lock);
+        g_tune_cache[key] = best;
+    }
+    return out ? exact_plan_get_tuning(plan, out) : EXACT_OK;
 }
 
 exact_status exact_forward(exact_plan_t plan, const float *x, float *z, exact_stream_t stream)
@@ -748,6 +867,9 @@ exact_status exact_adjoint(exact_plan_t plan, const float *r, float *g, exact_st
     memset(&a, 0, sizeof(a));
     a.rays = P.rays_f;
     a.walk = P.rays_w;
+    a.nsplit = P.adj_split;
+    a.split_part = P.split_part;
+    a.split_count = P.split_count;
     a.views = P.views;
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
@@ -794,6 +916,9 @@ exact_status exact_operator(exact_plan_t plan, const float *x, const void *y, ex
     memset(&a, 0, sizeof(a));
     a.rays = P.rays_f;
     a.walk = P.rays_w;
+    a.nsplit = P.adj_split;
+    a.split_part = P.split_part;
+    a.split_count = P.split_count;
     a.views = P.views;
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
@@ -885,6 +1010,9 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     memset(&a, 0, sizeof(a));
     a.rays = P.rays_f;
     a.walk = P.rays_w;
+    a.nsplit = P.adj_split;
+    a.split_part = P.split_part;
+    a.split_count = P.split_count;
     a.views = P.views;
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
@@ -1045,6 +1173,9 @@ exact_status exact_norm_estimate_f32(exact_plan_t plan, int max_iters, double rt
     memset(&a, 0, sizeof(a));
     a.rays = P.rays_f;
     a.walk = P.rays_w;
+    a.nsplit = P.adj_split;
+    a.split_part = P.split_part;
+    a.split_count = P.split_count;
     a.views = P.views;
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
@@ -1213,6 +1344,7 @@ struct exact_batch {
     cudaEvent_t staged = nullptr;
     bool staged_pending = false;
     int grid = 0;
+    int split_policy = 0;  // 0: one CTA per adjoint tile; 1: each plan's adj_split (exact_batch_autotune)
     std::vector<void *> captured_infos;  // info payloads of captured graphs
 };
 
@@ -1357,7 +1489,11 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
         J.iters = Jb.iters;
         J.check_every = Jb.opts.check_every;
         J.tol = Jb.opts.tol;
-        const int T = J.tiles_x * J.tiles_y, U = P.n_units;
+        J.nsplit = B->split_policy == 1 ? P.adj_split : 1;
+        J.a.nsplit = J.nsplit;
+        J.a.split_part = P.split_part;
+        J.a.split_count = P.split_count;
+        const int T = J.tiles_x * J.tiles_y * J.nsplit, U = P.n_units;  // adjoint items: (tile, split)
         const int per[5] = {U, T, U, T, 1};
         J.phase_off[0] = 0;
         for (int p = 0; p < 5; ++p) J.phase_off[p + 1] = J.phase_off[p] + per[p];
@@ -1403,6 +1539,70 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
         }
     }
     return EXACT_OK;
+}
+
+
+exact_status exact_batch_autotune(exact_batch_t B, const exact_job *jobs, int n_jobs, int *policy_out,
+                                  exact_stream_t stream)
+{
+    if (!B || !jobs || n_jobs < 1 || n_jobs > B->max_jobs) return EXACT_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<exact_job> trial(jobs, jobs + n_jobs);
+    for (exact_job &J : trial) {
+        exact_status st = check_plan(J.plan, true);
+        if (st != EXACT_OK) return st;
+        if (!J.x) return EXACT_ERR_INVALID_ARG;
+        J.iters = J.iters < 2 ? J.iters : 2;
+        J.info = nullptr;
+    }
+    // each job's x is saved in its plan's scratch image and put back after
+    // every trial, so the trials leave the jobs as they were
+    for (const exact_job &J : trial) {
+        const Plan &P = *reinterpret_cast<const Plan *>(J.plan);
+        EXACT_TRY(cudaMemcpyAsync(P.w32, J.x, sizeof(float) * (size_t)P.d, cudaMemcpyDeviceToDevice, s));
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return EXACT_ERR_CUDA;
+    }
+    const int keep = B->split_policy;
+    float best_ms = INFINITY;
+    int best = 0;
+    exact_status st = EXACT_OK;
+    for (int policy = 0; policy < 2 && st == EXACT_OK; ++policy) {
+        B->split_policy = policy;
+        float ms_min = INFINITY;
+        for (int rep = 0; rep < 3 && st == EXACT_OK; ++rep) {
+            float ms = 0.0f;
+            cudaError_t e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) st = exact_batch_solve(B, trial.data(), n_jobs, stream);
+            if (e == cudaSuccess && st == EXACT_OK) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess && st == EXACT_OK) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess && st == EXACT_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) st = cuda_status(e);
+            for (const exact_job &J : trial) {
+                if (st != EXACT_OK) break;
+                const Plan &P = *reinterpret_cast<const Plan *>(J.plan);
+                e = cudaMemcpyAsync(J.x, P.w32, sizeof(float) * (size_t)P.d, cudaMemcpyDeviceToDevice, s);
+                if (e != cudaSuccess) st = cuda_status(e);
+            }
+            if (rep > 0 && ms < ms_min) ms_min = ms;  // the first run of a policy warms up
+        }
+        if (st == EXACT_OK && ms_min < 0.97f * best_ms) {
+            best_ms = ms_min;
+            best = policy;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == EXACT_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_status(e);
+    }
+    B->split_policy = st == EXACT_OK ? best : keep;
+    if (policy_out) *policy_out = B->split_policy;
+    return st;
 }
 
 }  // extern "C"

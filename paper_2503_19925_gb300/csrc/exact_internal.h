@@ -132,6 +132,9 @@ struct Plan {
     double *tv_lam = nullptr;            // [2] lam carried by the half- and full-step projections
     void *tv_ws = nullptr;               // workspace of the TV-ball projection
     int tv_grid = 0;                     // its cooperative grid
+    float *split_part = nullptr;         // adjoint view split: partial tiles [tiles][kMaxSplit][kTH * kTW]
+    int *split_count = nullptr;          // [tiles] arrival counts (zeroed when the workspace is bound)
+    int adj_split = 1;                   // CTAs per adjoint tile (exact_plan_autotune / set_tuning)
     double *xrd = nullptr, *xcd = nullptr;  // FP64 padded copies (power iteration)
     double *zd = nullptr;                // FP64 projections [n]
     float *w32 = nullptr;                // FP32 power-iteration image [d]
@@ -225,8 +228,15 @@ struct AdjArgs {
     float *hist;
     int hist_put, hist_drop;
     double inv_m, inv_m_prev;
+    // view split over CTAs (nsplit <= 1: one CTA per tile): partial tiles
+    // [tiles][nsplit][kTH * kTW] and per-tile arrival counts (zero between launches)
+    int nsplit;
+    float *split_part;
+    int *split_count;
     const DevState *state;
 };
+
+constexpr int kMaxSplit = 8;  // view split of the adjoint (autotuned per plan)
 
 // One job of the persistent multi-job kernel (k_batch.cu).  A round of a job
 // is one extragradient iteration: phase 0 forward+link on x_t (n_units items),
@@ -240,7 +250,7 @@ struct BatchJob {
     const CUtensorMap *maps;   // [4] in global memory: rows 0, cols 0, rows 1, cols 1
     const LinkCoef *coef;      // global memory
     DevState *state;
-    int n_units, tiles_x, tiles_y, fan;
+    int n_units, tiles_x, tiles_y, fan, nsplit;
     int iters, check_every;
     double tol;
     int phase_off[6];          // items of the job before phase p within a round; [5] = items per round

@@ -269,11 +269,18 @@ __device__ __forceinline__ void strip_walk(const RayF *__restrict__ vrays, const
 }
 
 // A^T r over tile (bx, by) with the epilogue of MODE (see k_adjoint.cu).
-// blk is the tile's index for the partial norms.  Uses G warps (2G half-warps,
-// half-warp q takes views q, q + 2G, ...).
+// blk is the tile's index (partial norms, split bookkeeping).  The views are
+// split over a.nsplit CTAs (split index z) and, inside one, over its G warps:
+// half-warp q of split z takes views (z G + g) 2 + h + k 2 G nsplit.  With
+// nsplit > 1 each CTA leaves its partial tile in a.split_part; the last of
+// the tile's CTAs to finish (counted in a.split_count, which it resets) adds
+// the partials in split order and runs the epilogue, so the sum is the same
+// on every run.
 template <int MODE, bool FAN, bool DELTA, int G, bool COHERENT>
-__device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, long long blk, AdjSmem<G> &sm)
+__device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, long long blk, AdjSmem<G> &sm,
+                                             int z = 0)
 {
+    __shared__ int s_last;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, l = lane & 15;
     float *accx = sm.acc[g][0];
     float *accy = sm.acc[g][1];
@@ -293,7 +300,8 @@ __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, l
     const bool yok = ry < a.ny;
     const float fry = (float)ry, fx_lo = (float)(tx0 - 1), fx_hi = (float)min(tx0 + kTW, a.nx);
 
-    for (int v = 2 * g + (lane >> 4); v < a.n_views; v += 2 * G) {
+    const int nsplit = a.nsplit > 1 ? a.nsplit : 1;
+    for (int v = (z * G + g) * 2 + (lane >> 4); v < a.n_views; v += 2 * G * nsplit) {
         const ViewRec vr = a.views[v];
         const long long vb = (long long)v * a.n_bins;
         const RayF *vrays = a.rays + vb;
@@ -327,12 +335,38 @@ __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, l
         sm.stage[rl][k] = s;
     }
     __syncthreads();
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
         const int px = t % kTW, py = t / kTW;
         float gsum = sm.stage[py][px];
         for (int q = 0; q < G; ++q)
             gsum += sm.acc[q][0][(py + 1) * kAccLd + px] + sm.acc[q][0][(py + 1) * kAccLd + 16 + px];
+        sm.stage[py][px] = gsum;
+    }
+    __syncthreads();
+    if (nsplit > 1) {
+        float *mine = a.split_part + ((long long)blk * nsplit + z) * (kTH * kTW);
+        for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) mine[t] = sm.stage[t / kTW][t % kTW];
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_last = atomicAdd(a.split_count + blk, 1) == nsplit - 1;
+            if (s_last) atomicExch(a.split_count + blk, 0);
+        }
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        const float *all = a.split_part + (long long)blk * nsplit * (kTH * kTW);
+        for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
+            float v = 0.0f;
+            for (int q = 0; q < nsplit; ++q) v += __ldcg(all + (long long)q * (kTH * kTW) + t);
+            sm.stage[t / kTW][t % kTW] = v;
+        }
+        __syncthreads();
+    }
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
+        const int px = t % kTW, py = t / kTW;
+        const float gsum = sm.stage[py][px];
         const int kx = tx0 + px, ky = ty0 + py;
         const bool inside = kx < a.nx && ky < a.ny;
         if (MODE == ADJ_PLAIN) {

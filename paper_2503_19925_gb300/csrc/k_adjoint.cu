@@ -47,13 +47,13 @@ __global__ void __launch_bounds__(kG * 32, 7) k_adjoint(AdjArgs a)
     extern __shared__ __align__(16) unsigned char adj_smem[];
     AdjSmem<kG> &sm = *reinterpret_cast<AdjSmem<kG> *>(adj_smem);
     adjoint_tile<MODE, FAN, DELTA, kG, false>(a, blockIdx.x, blockIdx.y,
-                                              (long long)blockIdx.y * gridDim.x + blockIdx.x, sm);
+                                              (long long)blockIdx.y * gridDim.x + blockIdx.x, sm, blockIdx.z);
 }
 
 template <int MODE, bool FAN, bool DELTA>
 cudaError_t launch_adj(const AdjArgs &a, cudaStream_t s)
 {
-    const dim3 grid((a.nx + kTW - 1) / kTW, (a.ny + kTH - 1) / kTH);
+    const dim3 grid((a.nx + kTW - 1) / kTW, (a.ny + kTH - 1) / kTH, a.nsplit > 1 ? a.nsplit : 1);
     k_adjoint<MODE, FAN, DELTA><<<grid, kG * 32, sizeof(AdjSmem<kG>), s>>>(a);
     return cudaGetLastError();
 }

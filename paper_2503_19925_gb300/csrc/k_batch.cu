@@ -165,17 +165,25 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
             } else if (phase == 1 || phase == 3) {
                 AdjArgs a = J.a;
                 a.iter = round;
-                const int bx = local % J.tiles_x, by = local / J.tiles_x;
-                if (phase == 1) {
+                // item = (tile, split index): the tile's split CTAs combine
+                const int ns = J.nsplit > 1 ? J.nsplit : 1;
+                const int tile = local / ns, zsp = local - tile * ns;
+                const int bx = tile % J.tiles_x, by = tile / J.tiles_x;
+                if (by >= J.tiles_y) {  // a damaged item table: report and touch nothing
+                    if (t == 0) {
+                        J.state->status = EXACT_ERR_INVALID_ARG;
+                        J.state->done = 1;
+                    }
+                } else if (phase == 1) {
                     a.out_r = J.xr[1];
                     a.out_c = J.xc[1];
-                    if (J.fan) adjoint_tile<ADJ_EG, true, false, kBG, true>(a, bx, by, local, sm.u.adj);
-                    else adjoint_tile<ADJ_EG, false, false, kBG, true>(a, bx, by, local, sm.u.adj);
+                    if (J.fan) adjoint_tile<ADJ_EG, true, false, kBG, true>(a, bx, by, tile, sm.u.adj, zsp);
+                    else adjoint_tile<ADJ_EG, false, false, kBG, true>(a, bx, by, tile, sm.u.adj, zsp);
                 } else {
                     a.out_r = J.xr[0];
                     a.out_c = J.xc[0];
-                    if (J.fan) adjoint_tile<ADJ_EG_FINAL, true, false, kBG, true>(a, bx, by, local, sm.u.adj);
-                    else adjoint_tile<ADJ_EG_FINAL, false, false, kBG, true>(a, bx, by, local, sm.u.adj);
+                    if (J.fan) adjoint_tile<ADJ_EG_FINAL, true, false, kBG, true>(a, bx, by, tile, sm.u.adj, zsp);
+                    else adjoint_tile<ADJ_EG_FINAL, false, false, kBG, true>(a, bx, by, tile, sm.u.adj, zsp);
                 }
             } else {
                 batch_reduce(J, round, reinterpret_cast<double *>(&sm.u));

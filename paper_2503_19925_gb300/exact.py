@@ -56,6 +56,10 @@ class _TvInfo(ctypes.Structure):
                 ("status", ctypes.c_int)]
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("adj_split", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_double), ("hi", ctypes.c_double), ("tol", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("average_tail", ctypes.c_int), ("stop_rule", ctypes.c_int),
@@ -102,6 +106,9 @@ _SIGS = [
     ("exact_recommended_eta", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double,
                                              ctypes.POINTER(ctypes.c_double)]),
     ("exact_plan_nnz", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    ("exact_plan_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(_Tuning)]),
+    ("exact_plan_set_tuning", ctypes.c_int, [_VP, ctypes.POINTER(_Tuning)]),
+    ("exact_plan_autotune", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_Tuning), _VP]),
     ("exact_tv_opts_default", _TvOpts, []),
     ("exact_tv_workspace_bytes", ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
     ("exact_tv_project", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, ctypes.c_double, ctypes.c_double,
@@ -111,6 +118,8 @@ _SIGS = [
     ("exact_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_VP)]),
     ("exact_batch_destroy", ctypes.c_int, [_VP]),
     ("exact_batch_solve", ctypes.c_int, [_VP, ctypes.POINTER(_Job), ctypes.c_int, _VP]),
+    ("exact_batch_autotune", ctypes.c_int, [_VP, ctypes.POINTER(_Job), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            _VP]),
     ("exact_profile_enable", ctypes.c_int, [_VP, ctypes.c_int]),
     ("exact_profile_read", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     ("exact_status_string", _CP, [ctypes.c_int]),
@@ -379,6 +388,26 @@ class Plan:
         _check("exact_plan_set_background", load().exact_plan_set_background(self._h, M, arr, _ptr(p)))
         self._bg = p
 
+    @property
+    def tuning(self) -> dict:
+        """Kernel tuning of this plan (exact_plan_get_tuning)."""
+        t = _Tuning()
+        _check("exact_plan_get_tuning", load().exact_plan_get_tuning(self._h, ctypes.byref(t)))
+        return {"adj_split": t.adj_split}
+
+    def set_tuning(self, adj_split: int):
+        t = _Tuning()
+        t.adj_split = int(adj_split)
+        _check("exact_plan_set_tuning", load().exact_plan_set_tuning(self._h, ctypes.byref(t)))
+
+    def autotune(self, force: bool = False) -> dict:
+        """Time the kernel variants on this geometry and keep the fastest
+        (exact_plan_autotune; cached per geometry shape in this process)."""
+        t = _Tuning()
+        _check("exact_plan_autotune", load().exact_plan_autotune(self._h, int(bool(force)), ctypes.byref(t),
+                                                                 _stream()))
+        return {"adj_split": t.adj_split}
+
     def nnz(self) -> int:
         """Nonzero entries of A (counted on the host, cached)."""
         v = ctypes.c_longlong()
@@ -460,9 +489,7 @@ class Batch:
         except Exception:
             pass
 
-    def solve(self, jobs: list[Job], sync: bool = True):
-        """Run all jobs in one persistent launch; returns the list of SolveInfo
-        (filled once the stream passes the end of the batch) and the images."""
+    def _jobs(self, jobs: list[Job]):
         n = len(jobs)
         arr = (_Job * n)()
         infos = [_SolveInfo() for _ in range(n)]
@@ -477,6 +504,22 @@ class Batch:
                           _SolveOpts(float(jb.lo), float(jb.hi), float(jb.tol), int(jb.check_every), 0, 0, 0, None,
                                      0.0, tv_options(None)),
                           x.data_ptr(), ctypes.pointer(infos[k]))
+        return arr, infos, xs
+
+    def autotune(self, jobs: list[Job]) -> int:
+        """Pick this context's adjoint split policy by timing these jobs
+        (exact_batch_autotune; the jobs' images are left as they were)."""
+        arr, _, _ = self._jobs(jobs)
+        policy = ctypes.c_int(0)
+        _check("exact_batch_autotune", load().exact_batch_autotune(self._h, arr, len(jobs), ctypes.byref(policy),
+                                                                   _stream()))
+        return policy.value
+
+    def solve(self, jobs: list[Job], sync: bool = True):
+        """Run all jobs in one persistent launch; returns the list of SolveInfo
+        (filled once the stream passes the end of the batch) and the images."""
+        n = len(jobs)
+        arr, infos, xs = self._jobs(jobs)
         _check("exact_batch_solve", load().exact_batch_solve(self._h, arr, n, _stream()))
         if torch.cuda.is_current_stream_capturing():
             # a captured graph writes `infos` on every replay: keep them alive

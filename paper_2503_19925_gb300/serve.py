@@ -11,7 +11,8 @@ persistent launch (exact_batch_solve); a job resumes from its own iterate, so a
 round boundary changes nothing in its arithmetic.  After a round the loop reads
 each job's residual, retires the converged ones (their memory is freed) and
 admits new arrivals, which therefore overlap on the device with the jobs
-already running.
+already running.  Each plan takes the autotuned kernel split of its geometry
+shape (timed on the first request of a shape, cached afterwards).
 
 This is host orchestration only: all arithmetic runs in libexact.so.
 """
@@ -122,6 +123,7 @@ class Server:
             plan = Plan(req.geometry, req.mu, req.S)
             y = req.y.to(plan.device, non_blocking=True).contiguous()
             x = torch.zeros(plan.shape_img, dtype=torch.float32, device=plan.device)
+            plan.autotune()  # timed once per geometry shape, then cached
             lam, _ = plan.norm_estimate_f32(self.norm_iters, self.norm_rtol)
             eta = plan.recommended_eta(req.I0, lam)
             self.active.append(_Active(req, plan, y, x, eta, need, 0, self.now()))
@@ -196,6 +198,7 @@ def serve_sequential(requests: list[Request], realtime: bool = True, norm_iters:
         admitted = time.perf_counter() - t0
         plan = Plan(req.geometry, req.mu, req.S)
         y = req.y.to(plan.device).contiguous()
+        plan.autotune()
         lam, _ = plan.norm_estimate_f32(norm_iters, norm_rtol)
         eta = plan.recommended_eta(req.I0, lam)
         x, info = plan.solve(y, req.I0, eta, req.max_iters, lo=req.lo, hi=req.hi, tol=req.tol,

@@ -27,6 +27,10 @@ class FakePlan:
         self.closed = False
         FakePlan.live += 1
 
+    def autotune(self, force=False):
+        self.tuned = True
+        return {"adj_split": 1}
+
     def norm_estimate_f32(self, iters, rtol):
         return 100.0, 5
 
