@@ -57,6 +57,7 @@ def parse_args(argv=None):
     p.add_argument("--batch-iters", type=int, default=None)
     p.add_argument("--no-served", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-tv", action="store_true", help="skip the TV-ball feasible-set measurement")
+    p.add_argument("--no-gaussian", action="store_true", help="skip the Gaussian-model (Fig. 6) measurement")
     p.add_argument("--serve-jobs", type=int, default=32)
     p.add_argument("--serve-loads", default="0.8,1.5",
                    help="arrival rates as fractions of the measured sequential capacity")
@@ -420,6 +421,36 @@ def run_tv(ex, torch, dev, rank: int):
     return out
 
 
+def run_gaussian(ex, torch, dev):
+    """The experiment of Sec. 3.2 / Fig. 6 on the GPU (dense FP64 path):
+    Gaussian a_i, noiseless monochromatic counts (I0 = 1, mu = 1), d = 100,
+    ||x*|| = 3, step 0.25, no projection, n in {5, 10, 20, 40, 80} d.  Reports
+    the iterations to an error of 1e-8 and 1e-12 ||x*|| and the time per
+    iteration."""
+    d, norm, step, max_iters = 100, 3.0, 0.25, 15000
+    out = []
+    for mult in (5, 10, 20, 40, 80):
+        A, xs = synth.gaussian_case(mult * d, d, norm, seed=mult)
+        y = np.exp(-np.maximum(A @ xs, 0.0))
+        D = ex.Dense(torch.tensor(A, dtype=torch.float64, device=dev), [1.0], [[1.0]])
+        yt = torch.tensor(y[None], dtype=torch.float64, device=dev)
+        xt = torch.tensor(xs, dtype=torch.float64, device=dev)
+        D.solve(yt, 1.0, step, 10, x_true=xt)  # warm
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, err = D.solve(yt, 1.0, step, max_iters, x_true=xt)
+        b.record()
+        b.synchronize()
+        e = err.cpu().numpy()
+        hit = lambda thr: int(np.argmax(e < thr)) + 1 if (e < thr).any() else None
+        out.append({"n_over_d": mult, "iters_to_1e-8": hit(1e-8), "iters_to_machine_precision": hit(1e-12 * norm),
+                    "final_error": float(e[-1]), "us_per_iter": 1e3 * a.elapsed_time(b) / max_iters})
+        D.close()
+    return {"workload": "Sec. 3.2 / Fig. 6: Gaussian a_i, noiseless, I0 = 1, mu = 1, d = 100, ||x*|| = 3, "
+                        "step 0.25, no projection, FP64", "max_iters": max_iters, "points": out}
+
+
 def run_batched(ex, torch, dev, n_jobs: int, iters: int, rank: int):
     """The batched mix: n_jobs reconstructions of uneven size/views/windows,
     (a) one after another with exact_solve, (b) in one persistent launch with
@@ -660,6 +691,8 @@ def run_exact(args):
                                     [float(v) for v in args.serve_loads.split(",") if v], rank)
     if not args.no_tv:
         line["tv"] = run_tv(ex, torch, dev, rank)
+    if not args.no_gaussian:
+        line["gaussian"] = run_gaussian(ex, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_baseline_iters)
     if rank == 0:

@@ -179,6 +179,34 @@ exact_status exact_tv_project(int nx, int ny, const float *z, double tau, double
                               const exact_tv_opts *opts, float *x, void *workspace, size_t workspace_bytes,
                               exact_tv_info *info, exact_stream_t stream);
 
+/* ---- Dense measurement vectors (Sec. 2.2, Gaussian model; Sec. 3.2, Fig. 6) ----
+ * The operator of Eq. (8) with an explicit FP64 matrix A whose rows are the
+ * measurement vectors a_i (i.i.d. N(0, I_d) in the Gaussian model):
+ *   F(x) = (1/(W n)) sum_{w,i} (y_{w,i} - I0 h_w(<a_i, x>)) a_i,
+ * h_w as in Eq. (7) (the ReLU of Eq. (4) matters here: <a_i, x> can be
+ * negative).  All arithmetic is FP64 (Fig. 6 follows the error to machine
+ * precision); every sum has a fixed order. */
+typedef struct exact_dense *exact_dense_t;
+
+/* A: caller-owned device [n][d] FP64, row-major, kept by pointer (it must
+ * outlive the context and not change while work using it is in flight);
+ * spectrum and windows as in exact_plan_create (copied).  The context
+ * allocates its own scratch (8 (W K + K + n + d + ceil(n/64) d) bytes). */
+exact_status exact_dense_create(int n, int d, const double *A, const exact_spectrum *spectrum,
+                                const exact_windows *windows, exact_dense_t *out);
+exact_status exact_dense_destroy(exact_dense_t dense);
+
+/* F(x): x device [d], y device [W][n], F device [d], all FP64. */
+exact_status exact_dense_operator(exact_dense_t dense, const double *x, const double *y, double I0, double *F,
+                                  exact_stream_t stream);
+
+/* `iters` iterations of Eq. (11) on the box [lo, hi]^d (lo = -inf, hi = +inf:
+ * no projection, as in Sec. 3.2) in place on x (device [d]).  If x_true
+ * (device [d]) is given, err (device [iters]) receives ||x_t - x_true|| after
+ * iteration t (both NULL otherwise).  Asynchronous on stream. */
+exact_status exact_dense_solve(exact_dense_t dense, const double *y, double I0, double eta, int iters, double lo,
+                               double hi, double *x, const double *x_true, double *err, exact_stream_t stream);
+
 /* Kernel tuning of a plan (no counterpart in the paper: a property of this
  * implementation).  adj_split: CTAs sharing one 16 x 16-pixel tile of the
  * adjoint, each taking an interleaved subset of the views (1..8); the tile's

@@ -109,6 +109,12 @@ _SIGS = [
     ("exact_plan_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(_Tuning)]),
     ("exact_plan_set_tuning", ctypes.c_int, [_VP, ctypes.POINTER(_Tuning)]),
     ("exact_plan_autotune", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_Tuning), _VP]),
+    ("exact_dense_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, ctypes.POINTER(_Spectrum),
+                                          ctypes.POINTER(_Windows), ctypes.POINTER(_VP)]),
+    ("exact_dense_destroy", ctypes.c_int, [_VP]),
+    ("exact_dense_operator", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, _VP, _VP]),
+    ("exact_dense_solve", ctypes.c_int, [_VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, _VP, _VP, _VP, _VP]),
     ("exact_tv_opts_default", _TvOpts, []),
     ("exact_tv_workspace_bytes", ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
     ("exact_tv_project", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, ctypes.c_double, ctypes.c_double,
@@ -229,6 +235,68 @@ def tv_project(z: torch.Tensor, tau: float, lo: float = 0.0, hi: float = math.in
                                                     ctypes.byref(o), _ptr(x), _ptr(ws), nb, ctypes.byref(info),
                                                     _stream()))
     return x, TvInfo(info.rounds, info.solves, info.lam, info.status)
+
+
+class Dense:
+    """EXACT with an explicit FP64 measurement matrix A [n][d] on the device
+    (the Gaussian model of Sec. 2.2 / the experiment of Sec. 3.2); A must stay
+    alive and unchanged while the context is used."""
+
+    def __init__(self, A: torch.Tensor, mu, S):
+        lib = load()
+        if A.dtype != torch.float64 or A.dim() != 2 or not A.is_cuda or not A.is_contiguous():
+            raise ValueError("A must be a contiguous CUDA float64 [n][d] tensor")
+        self.A = A
+        self.n, self.d = A.shape
+        mu = [float(v) for v in mu]
+        rows = [[float(v) for v in r] for r in S]
+        self.W, self.K = len(rows), len(mu)
+        mu_arr = (ctypes.c_double * self.K)(*mu)
+        s_arr = (ctypes.c_double * (self.W * self.K))(*[v for r in rows for v in r])
+        h = ctypes.c_void_p()
+        _check("exact_dense_create", lib.exact_dense_create(self.n, self.d, _ptr(A), ctypes.byref(_Spectrum(self.K, mu_arr)),
+                                                            ctypes.byref(_Windows(self.W, s_arr)), ctypes.byref(h)))
+        self._h = h
+
+    def _v(self, t, size, name):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != size:
+            raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of {size} values")
+
+    def operator(self, x: torch.Tensor, y: torch.Tensor, I0: float) -> torch.Tensor:
+        self._v(x, self.d, "x")
+        self._v(y, self.W * self.n, "y")
+        F = torch.empty(self.d, dtype=torch.float64, device=self.A.device)
+        _check("exact_dense_operator", load().exact_dense_operator(self._h, _ptr(x), _ptr(y), float(I0), _ptr(F),
+                                                                   _stream()))
+        return F
+
+    def solve(self, y: torch.Tensor, I0: float, eta: float, iters: int, x: torch.Tensor | None = None,
+              lo: float = -math.inf, hi: float = math.inf, x_true: torch.Tensor | None = None):
+        """Returns (x, err) with err[t] = ||x_t - x_true|| (None without x_true)."""
+        self._v(y, self.W * self.n, "y")
+        if x is None:
+            x = torch.zeros(self.d, dtype=torch.float64, device=self.A.device)
+        self._v(x, self.d, "x")
+        err = None
+        if x_true is not None:
+            self._v(x_true, self.d, "x_true")
+            err = torch.empty(max(int(iters), 1), dtype=torch.float64, device=self.A.device)
+        _check("exact_dense_solve", load().exact_dense_solve(self._h, _ptr(y), float(I0), float(eta), int(iters),
+                                                             float(lo), float(hi), _ptr(x),
+                                                             None if x_true is None else _ptr(x_true),
+                                                             None if err is None else _ptr(err), _stream()))
+        return x, (err[: int(iters)] if err is not None else None)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().exact_dense_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

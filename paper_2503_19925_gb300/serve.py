@@ -11,8 +11,8 @@ persistent launch (exact_batch_solve); a job resumes from its own iterate, so a
 round boundary changes nothing in its arithmetic.  After a round the loop reads
 each job's residual, retires the converged ones (their memory is freed) and
 admits new arrivals, which therefore overlap on the device with the jobs
-already running.  Each plan takes the autotuned kernel split of its geometry
-shape (timed on the first request of a shape, cached afterwards).
+already running.  (The batch runs one CTA per adjoint tile, so the per-plan
+autotuner is not needed here; the one-at-a-time baseline below uses it.)
 
 This is host orchestration only: all arithmetic runs in libexact.so.
 """
@@ -123,7 +123,6 @@ class Server:
             plan = Plan(req.geometry, req.mu, req.S)
             y = req.y.to(plan.device, non_blocking=True).contiguous()
             x = torch.zeros(plan.shape_img, dtype=torch.float32, device=plan.device)
-            plan.autotune()  # timed once per geometry shape, then cached
             lam, _ = plan.norm_estimate_f32(self.norm_iters, self.norm_rtol)
             eta = plan.recommended_eta(req.I0, lam)
             self.active.append(_Active(req, plan, y, x, eta, need, 0, self.now()))
@@ -184,7 +183,8 @@ class Server:
 def serve_sequential(requests: list[Request], realtime: bool = True, norm_iters: int = 60,
                      norm_rtol: float = 1e-5) -> list[Result]:
     """The plain baseline: first come, first served, each request solved alone
-    with exact_solve (same tolerance test every check_every iterations)."""
+    with exact_solve (same tolerance test every check_every iterations), each
+    plan with the autotuned adjoint split of its shape."""
     pending = deque(sorted(requests, key=lambda r: r.arrival))
     out = []
     t0 = time.perf_counter()
