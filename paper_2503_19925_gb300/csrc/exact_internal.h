@@ -78,6 +78,7 @@ struct __align__(16) ViewRec {
 // adding kPad, as the tensor-map x coordinate must be 16-byte aligned).
 constexpr int kFR = 128;   // rays per unit (threads per CTA)
 constexpr int kFC = 16;    // driving lines per staged chunk
+constexpr int kFStages = 2;  // staging buffers (copies kFStages - 1 chunks ahead)
 constexpr int kFHB = 256;  // staged cross-axis rows per chunk (tensor-map box height)
 // Adjoint tile (pixels): one CTA gathers A^T r over kTW x kTH pixels.
 constexpr int kTW = 16;

@@ -69,22 +69,23 @@ __device__ __forceinline__ float ld_dyn(const float *p)
 // mbarriers and the broadcast flag live outside so that a persistent kernel can
 // reuse this space for other items.
 struct FwdSmem {
-    float buf[2][kFC * kFHB];
+    float buf[kFStages][kFC * kFHB];
 };
 
 // ------------------------------------------------------------------ forward
 
 // Joseph forward walk of work unit `ui` (see k_forward.cu for the design).
-// Thread 0 issues the copies; every thread waits on the two mbarriers and
-// keeps ph[b], the completed phases of barrier b across calls (both start at 0
-// after mbar_init).  One CTA barrier per chunk.  Returns false (uniformly) if
-// a staging copy timed out; the caller must then stop using the shared
-// buffers.  The buffers may still be read by other threads when it returns:
-// the caller synchronises the CTA before the next unit.
+// Thread 0 issues the copies, kFStages - 1 chunks ahead; every thread waits on
+// the chunk's mbarrier and keeps in bit b of `phase` the parity of the
+// completed phases of barrier b across calls (all 0 after mbar_init).  One
+// CTA barrier per chunk.  Returns false (uniformly) if a staging copy timed
+// out; the caller must then stop using the shared buffers.  The buffers may
+// still be read by other threads when it returns: the caller synchronises the
+// CTA before the next unit.
 template <bool LINK, bool COHERENT>
 __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUtensorMap *map_r,
                                              const CUtensorMap *map_c, const LinkCoef *coef, FwdSmem &sm,
-                                             uint64_t *bar, uint32_t (&ph)[2])
+                                             uint64_t *bar, uint32_t &phase)
 {
     const FwdUnit u = a.units[ui];
     const int t = threadIdx.x;
@@ -103,24 +104,27 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
 
     if (t == 0 && u.nchunks > 0) {
         // order earlier generic accesses of the buffers (and of global data
-        // synchronised with other CTAs) before the async-proxy copy
+        // synchronised with other CTAs) before the async-proxy copies
         asm volatile("fence.proxy.async;" ::: "memory");
-        tma_box(sm.buf[0], map, kst[0] + kPad, u.jc0 * kFC, &bar[0]);
+        for (int c = 0; c < kFStages - 1 && c < u.nchunks; ++c)
+            tma_box(sm.buf[c], map, kst[c] + kPad, (u.jc0 + c) * kFC, &bar[c]);
     }
     float acc = 0.0f;
+    int b = 0;  // stage of chunk c
     for (int c = 0; c < u.nchunks; ++c) {
-        const int b = c & 1;
         // every thread waits for chunk c; the barrier then also tells that all
         // threads are done with chunk c - 1, whose buffer the next copy reuses
-        // (ph indexed with constants so that it stays in registers)
-        bool ok = mbar_wait(&bar[b], (b ? ph[1] : ph[0]) & 1u);
+        bool ok = mbar_wait(&bar[b], (phase >> b) & 1u);
         ok = __syncthreads_and(ok) != 0;
         if (!ok) {
-            // the copy of chunk c did not complete in time everywhere: report,
-            // wait (bounded) for it once more so no copy lands after the
+            // a copy did not complete in time everywhere: report, wait
+            // (bounded) for every copy in flight so none lands after the
             // buffers are released
             if (t == 0) {
-                mbar_wait(&bar[b], (b ? ph[1] : ph[0]) & 1u);
+                for (int q = c; q < u.nchunks && q < c + kFStages - 1; ++q) {
+                    const int bq = q % kFStages;
+                    mbar_wait(&bar[bq], (phase >> bq) & 1u);
+                }
                 if (a.err) {
                     a.err->status = EXACT_ERR_TIMEOUT;
                     a.err->done = 1;
@@ -128,13 +132,14 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
             }
             return false;
         }
-        if (b) ph[1] += 1;
-        else ph[0] += 1;
-        if (t == 0 && c + 1 < u.nchunks) {
-            // the other buffer was last read in chunk c - 1 (before the
-            // barrier above); order those reads before the async-proxy write
+        phase ^= 1u << b;
+        const int cn = c + kFStages - 1;
+        if (t == 0 && cn < u.nchunks) {
+            // that buffer was last read in chunk c - 1 (before the barrier
+            // above); order those reads before the async-proxy write
+            const int bn = cn % kFStages;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tma_box(sm.buf[b ^ 1], map, kst[c + 1] + kPad, (u.jc0 + c + 1) * kFC, &bar[b ^ 1]);
+            tma_box(sm.buf[bn], map, kst[cn] + kPad, (u.jc0 + cn) * kFC, &bar[bn]);
         }
         const int j0 = (u.jc0 + c) * kFC;
         const int ja = max(jlo, j0), jb = min(jhi, j0 + kFC - 1);
@@ -166,6 +171,7 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
                 di += 1.0f;
             }
         }
+        b = b + 1 == kFStages ? 0 : b + 1;
     }
     // the caller synchronises the CTA before the buffers are used again
     if (!has_ray) return true;

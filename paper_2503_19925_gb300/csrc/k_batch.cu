@@ -43,7 +43,7 @@ struct __align__(128) BatchSmem {
         FwdSmem fwd;
         AdjSmem<kBG> adj;
     } u;
-    uint64_t bar[2];
+    uint64_t bar[kFStages];
     int prefix[5 * kMaxBatch + 1];
     unsigned long long item;
     int ok;
@@ -103,14 +103,13 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
     const int nseg = 5 * n_jobs;
     for (int i = t; i <= nseg; i += kBatchThreads) sm.prefix[i] = prefix_g[i];
     if (t == 0) {
-        mbar_init(&sm.bar[0]);
-        mbar_init(&sm.bar[1]);
+        for (int q = 0; q < kFStages; ++q) mbar_init(&sm.bar[q]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const unsigned long long per_round = (unsigned long long)sm.prefix[nseg];
     const unsigned long long total = per_round * (unsigned long long)rounds;
-    uint32_t ph[2] = {0u, 0u};
+    uint32_t fphase = 0u;  // staging-barrier parities of the forward items
 
     for (;;) {
         if (t == 0) sm.item = atomicAdd(next, 1ULL);
@@ -161,7 +160,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
                 FwdArgs f = J.f;
                 f.img = J.img[q];
                 item_ok = forward_unit<true, true>(f, local, J.maps + 2 * q, J.maps + 2 * q + 1, J.coef, sm.u.fwd,
-                                                   sm.bar, ph);
+                                                   sm.bar, fphase);
             } else if (phase == 1 || phase == 3) {
                 AdjArgs a = J.a;
                 a.iter = round;

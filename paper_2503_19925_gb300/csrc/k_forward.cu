@@ -45,15 +45,14 @@ __global__ void __launch_bounds__(kFR) k_forward_tma(FwdArgs a, const __grid_con
 {
     if (a.state && a.state->done) return;
     __shared__ __align__(128) FwdSmem sm;
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[kFStages];
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0]);
-        mbar_init(&bar[1]);
+        for (int q = 0; q < kFStages; ++q) mbar_init(&bar[q]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    uint32_t ph[2] = {0u, 0u};
-    forward_unit<LINK, false>(a, blockIdx.x, &map_r, &map_c, &coef, sm, bar, ph);
+    uint32_t phase = 0u;
+    forward_unit<LINK, false>(a, blockIdx.x, &map_r, &map_c, &coef, sm, bar, phase);
 }
 
 // FP64 forward of the power iteration: z = inv_norm * A w, plus per-block
