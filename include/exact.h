@@ -230,6 +230,13 @@ exact_status exact_plan_set_tuning(exact_plan_t plan, const exact_tuning *tuning
  * synchronises the stream. */
 exact_status exact_plan_autotune(exact_plan_t plan, int force, exact_tuning *out, exact_stream_t stream);
 
+/* argmin_x ||x - z||^2 + lam ||x||_TV (the TV-regularised problem of Sec. 3.1,
+ * and the step of the proximal variant of Sec. 5), by fgp_iters steps of the
+ * fast gradient projection method from a zero dual.  z, x: device [ny][nx]
+ * FP32, distinct; lam > 0; workspace as for exact_tv_project.  Synchronises. */
+exact_status exact_tv_prox(int nx, int ny, const float *z, double lam, int fgp_iters, float *x, void *workspace,
+                           size_t workspace_bytes, exact_stream_t stream);
+
 /* Stopping rules of exact_solve (see exact_solve_opts). */
 typedef enum {
     EXACT_STOP_RESIDUAL = 0, /* relative change of the iterate */
@@ -242,7 +249,13 @@ typedef enum {
  * Sec. 3.1 (each half and full step then projects with exact_tv_project's
  * algorithm, the bisection of each of the two projections starting from its
  * lam of the previous iteration; average_tail must be 0, else
- * EXACT_ERR_UNSUPPORTED).  Iterations are counted
+ * EXACT_ERR_UNSUPPORTED).  prox_lambda > 0 selects the proximal variant the
+ * Discussion (Sec. 5) proposes instead of the projection:
+ *   x_{t+1/2} = argmin_x ||x - (x_t - eta F(x_t))||^2 + prox_lambda ||x||_TV,
+ *   x_{t+1}   = argmin_x ||x - (x_t - eta F(x_{t+1/2}))||^2 + prox_lambda ||x||_TV,
+ * each solved by tv.fgp_iters dual steps from a zero dual (exact_tv_prox);
+ * there is no constraint then (lo, hi only clamp x_1; tv_bound must be 0).
+ * Iterations are counted
  * t = 1, 2, ...; x_t is the iterate after t of them.
  *  - stop_rule EXACT_STOP_RESIDUAL: if tol > 0 and check_every > 0 the solve
  *    stops after the first t that is a multiple of check_every with
@@ -268,6 +281,7 @@ typedef struct {
     float *history;  /* EXACT_STOP_AVERAGE: device ring [history_cap][ny][nx] */
     double tv_bound; /* > 0: X = {||x||_TV <= tv_bound} ∩ [lo, hi]^d (see exact_tv_project) */
     exact_tv_opts tv; /* options of that projection */
+    double prox_lambda; /* > 0: the proximal variant of the Discussion (see below) */
 } exact_solve_opts;
 
 typedef struct {
@@ -280,7 +294,7 @@ typedef struct {
 
 /* Default options: lo = 0, hi = +inf, tol = 0, check_every = 1, average_tail = 0,
  * stop_rule = EXACT_STOP_RESIDUAL, no history, tv_bound = 0 (no TV ball),
- * tv = exact_tv_opts_default(). */
+ * tv = exact_tv_opts_default(), prox_lambda = 0. */
 exact_solve_opts exact_solve_opts_default(void);
 
 /* Projected extragradient, Eq. (11), with constant step eta:

@@ -210,3 +210,20 @@ def solve_tv(g, S, mu, I0: float, y, eta: float, iters: int, tau: float, lo: flo
             break
     out = (sum(window) / len(window)) if running_average and window else x
     return TvSolveResult(out, np.array(rel), lam_h, lam_f, t, np.array(changes) if running_average else None)
+
+
+def solve_prox_tv(g, S, mu, I0: float, y, eta: float, iters: int, lam: float, fgp_iters: int = 40, x1=None,
+                  lo: float = 0.0, hi: float = np.inf, bg=None) -> np.ndarray:
+    """The proximal variant of the extragradient iteration proposed in the
+    Discussion (Sec. 5), with l_X = ||.||_TV and a constant lam:
+        x_{t+1/2} = argmin_x ||x - (x_t - eta F(x_t))||^2 + lam ||x||_TV,
+        x_{t+1}   = argmin_x ||x - (x_t - eta F(x_{t+1/2}))||^2 + lam ||x||_TV,
+    each solved by prox_tv with fgp_iters steps from a zero dual.  There is no
+    constraint; x1 (default 0) is clamped to [lo, hi] once."""
+    import oracle
+    x = np.zeros((g.ny, g.nx)) if x1 is None else np.array(x1, dtype=np.float64).reshape(g.ny, g.nx)
+    x = np.clip(x, lo, hi)
+    for _ in range(iters):
+        xh, _, _ = prox_tv(x - eta * oracle.operator(g, x, S, mu, I0, y, bg), lam, fgp_iters)
+        x, _, _ = prox_tv(x - eta * oracle.operator(g, xh, S, mu, I0, y, bg), lam, fgp_iters)
+    return x

@@ -519,6 +519,7 @@ exact_solve_opts exact_solve_opts_default(void)
     o.history = nullptr;
     o.tv_bound = 0.0;
     o.tv = exact_tv_opts_default();
+    o.prox_lambda = 0.0;
     return o;
 }
 
@@ -948,7 +949,10 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     if (running && (o.average_tail || !o.history || o.history_cap < (iters / 2 > 1 ? iters / 2 : 1)))
         return EXACT_ERR_INVALID_ARG;
     if (isnan(o.tv_bound) || o.tv_bound < 0.0 || o.tv_bound == INFINITY) return EXACT_ERR_INVALID_ARG;
-    const bool tvb = o.tv_bound > 0.0;
+    if (isnan(o.prox_lambda) || o.prox_lambda < 0.0 || o.prox_lambda == INFINITY) return EXACT_ERR_INVALID_ARG;
+    const bool proxm = o.prox_lambda > 0.0;
+    if (proxm && o.tv_bound > 0.0) return EXACT_ERR_INVALID_ARG;
+    const bool tvb = o.tv_bound > 0.0 || proxm;  // both run the TV kernel after an unprojected step
     if (tvb && (o.tv.fgp_iters < 1 || o.tv.max_bisect < 1 || o.tv.max_dykstra < 0 || !(o.tv.tol_tv >= 0.0) ||
                 !(o.tv.tol_dykstra >= 0.0) || isnan(o.tv.lam0) || o.tv.lam0 == INFINITY))
         return EXACT_ERR_INVALID_ARG;
@@ -970,7 +974,7 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     TvLaunch tvl;
     memset(&tvl, 0, sizeof(tvl));
     if (tvb) {
-        const double lam2[2] = {o.tv.lam0, o.tv.lam0};
+        const double lam2[2] = {proxm ? o.prox_lambda : o.tv.lam0, proxm ? o.prox_lambda : o.tv.lam0};
         EXACT_TRY(cudaMemcpyAsync(P.tv_lam, lam2, sizeof(lam2), cudaMemcpyHostToDevice, s));
         tvl.nx = P.g.nx;
         tvl.ny = P.g.ny;
@@ -988,6 +992,7 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
         tvl.max_dykstra = o.tv.max_dykstra;
         tvl.lo = lo;
         tvl.hi = hi;
+        tvl.fixed_lam = proxm ? 1 : 0;
     }
 
     FwdArgs f;
@@ -1415,7 +1420,8 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
         if (isnan(o.lo) || isnan(o.hi) || o.lo > o.hi || o.lo == INFINITY || o.hi == -INFINITY)
             return EXACT_ERR_INVALID_ARG;
         if (!isfin(o.tol) || o.tol < 0.0 || o.check_every < 0) return EXACT_ERR_INVALID_ARG;
-        if (o.average_tail || o.stop_rule != EXACT_STOP_RESIDUAL || o.tv_bound != 0.0) return EXACT_ERR_UNSUPPORTED;
+        if (o.average_tail || o.stop_rule != EXACT_STOP_RESIDUAL || o.tv_bound != 0.0 || o.prox_lambda != 0.0)
+            return EXACT_ERR_UNSUPPORTED;
         for (int q = 0; q < j; ++q)
             if (jobs[q].plan == J.plan) return EXACT_ERR_INVALID_ARG;
         rounds = J.iters > rounds ? J.iters : rounds;

@@ -302,6 +302,7 @@ struct TvLaunch {
     double tau, tol_tv, tol_dykstra;
     int fgp_iters, max_bisect, max_dykstra;
     float lo, hi;
+    int fixed_lam;               // proximal mode: argmin ||x - z||^2 + lam TV(x), lam from lam_io
 };
 size_t tv_workspace_bytes(int nx, int ny, int grid);
 int tv_grid(long long d);

@@ -57,6 +57,7 @@ struct TvArgs {
     double tau, tol_tv, tol_dyk;
     int fgp_iters, max_bisect, max_dyk;
     float lo, hi;
+    int fixed_lam;         // proximal mode: one regularised solve with lam, no constraint
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
@@ -248,12 +249,16 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_project(TvArgs a)
         for (long long q = first; q < a.d; q += stride) a.w[q] = __ldcg(a.zk + q) + __ldcg(a.pk + q);
         if (!grid_barrier(a.bar, a.err, a.done)) return;
         double part = 0.0;
-        for (long long q = first; q < a.d; q += stride) part += tv_term(a.w, (int)(q / nx), (int)(q % nx), nx, ny);
-        const double tw = grid_sum(a, part, slot, ok);
-        slot ^= 1;
-        if (!ok) return;
+        double tw = 0.0;
+        if (!a.fixed_lam) {
+            for (long long q = first; q < a.d; q += stride)
+                part += tv_term(a.w, (int)(q / nx), (int)(q % nx), nx, ny);
+            tw = grid_sum(a, part, slot, ok);
+            slot ^= 1;
+            if (!ok) return;
+        }
         const float *ysrc = a.w;
-        if (tw > a.tau) {
+        if (tw > a.tau || a.fixed_lam) {
             double lo = 0.0, hi = INFINITY;
             for (int s = 0; s < a.max_bisect; ++s) {
                 const float theta = (float)(0.5 * lam);
@@ -279,6 +284,10 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_project(TvArgs a)
                 for (long long q = first; q < a.d; q += stride)
                     a.xt[q] = prox_x(a.w, px, py, theta, (int)(q / nx), (int)(q % nx), nx, ny);
                 if (!grid_barrier(a.bar, a.err, a.done)) return;
+                if (a.fixed_lam) {
+                    ++solves;
+                    break;
+                }
                 part = 0.0;
                 for (long long q = first; q < a.d; q += stride)
                     part += tv_term(a.xt, (int)(q / nx), (int)(q % nx), nx, ny);
@@ -424,8 +433,10 @@ cudaError_t launch_tv_project(const TvLaunch &L, cudaStream_t s)
     a.fgp_iters = L.fgp_iters;
     a.max_bisect = L.max_bisect;
     a.max_dyk = L.max_dykstra;
-    a.lo = L.lo;
-    a.hi = L.hi;
+    a.lo = L.fixed_lam ? -INFINITY : L.lo;
+    a.hi = L.fixed_lam ? INFINITY : L.hi;
+    a.fixed_lam = L.fixed_lam;
+    if (L.fixed_lam) a.max_dyk = 1;
     cudaError_t e = cudaMemsetAsync(tail->bar, 0, sizeof(tail->bar), s);
     if (e != cudaSuccess) return e;
     void *args[] = {&a};
@@ -505,6 +516,39 @@ exact_status exact_tv_project(int nx, int ny, const float *z, double tau, double
         info->lam = h.lam;
         info->status = (exact_status)h.status;
     }
+    return h.status == 0 ? EXACT_OK : (exact_status)h.status;
+}
+
+exact_status exact_tv_prox(int nx, int ny, const float *z, double lam, int fgp_iters, float *x, void *workspace,
+                           size_t workspace_bytes, exact_stream_t stream)
+{
+    if (nx < 1 || ny < 1 || nx > 16384 || ny > 16384 || !z || !x || !workspace || z == x) return EXACT_ERR_INVALID_ARG;
+    if (!(lam > 0.0) || !(lam < INFINITY) || fgp_iters < 1) return EXACT_ERR_INVALID_ARG;
+    const int grid = tv_grid((long long)nx * ny);
+    if (grid <= 0) return EXACT_ERR_CUDA;
+    if (workspace_bytes < tv_workspace_bytes(nx, ny, grid)) return EXACT_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    TvTail *tail = tv_tail(workspace, nx, ny, grid);
+    TvTail h;
+    memset(&h, 0, sizeof(h));
+    h.lam = lam;
+    if (cudaMemcpyAsync(tail, &h, sizeof(h), cudaMemcpyHostToDevice, s) != cudaSuccess) return EXACT_ERR_CUDA;
+    TvLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.nx = nx;
+    L.ny = ny;
+    L.grid = grid;
+    L.z = z;
+    L.out = x;
+    L.ws = workspace;
+    L.fgp_iters = fgp_iters;
+    L.max_bisect = 1;
+    L.max_dykstra = 1;
+    L.fixed_lam = 1;
+    cudaError_t e = launch_tv_project(L, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, tail, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? EXACT_ERR_OOM : EXACT_ERR_CUDA;
     return h.status == 0 ? EXACT_OK : (exact_status)h.status;
 }
 

@@ -64,7 +64,7 @@ class _SolveOpts(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_double), ("hi", ctypes.c_double), ("tol", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("average_tail", ctypes.c_int), ("stop_rule", ctypes.c_int),
                 ("history_cap", ctypes.c_int), ("history", ctypes.c_void_p), ("tv_bound", ctypes.c_double),
-                ("tv", _TvOpts)]
+                ("tv", _TvOpts), ("prox_lambda", ctypes.c_double)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -117,6 +117,8 @@ _SIGS = [
                                          ctypes.c_double, _VP, _VP, _VP, _VP]),
     ("exact_tv_opts_default", _TvOpts, []),
     ("exact_tv_workspace_bytes", ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+    ("exact_tv_prox", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, ctypes.c_double, ctypes.c_int, _VP, _VP,
+                                     ctypes.c_size_t, _VP]),
     ("exact_tv_project", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.POINTER(_TvOpts), _VP, _VP, ctypes.c_size_t,
                                         ctypes.POINTER(_TvInfo), _VP]),
@@ -299,6 +301,20 @@ class Dense:
             pass
 
 
+def tv_prox(z: torch.Tensor, lam: float, fgp_iters: int = 40, out: torch.Tensor | None = None) -> torch.Tensor:
+    """argmin_x ||x - z||^2 + lam ||x||_TV of the device image z (exact_tv_prox)."""
+    lib = load()
+    if z.dtype != torch.float32 or z.dim() != 2 or not z.is_cuda or not z.is_contiguous():
+        raise ValueError("z must be a contiguous CUDA float32 [ny][nx] tensor")
+    ny, nx = z.shape
+    nb = lib.exact_tv_workspace_bytes(nx, ny)
+    ws = torch.empty(nb, dtype=torch.uint8, device=z.device)
+    x = out if out is not None else torch.empty_like(z)
+    _check("exact_tv_prox", lib.exact_tv_prox(nx, ny, _ptr(z), float(lam), int(fgp_iters), _ptr(x), _ptr(ws), nb,
+                                              _stream()))
+    return x
+
+
 class Plan:
     """An EXACT plan on the current CUDA device, with its workspace.
 
@@ -391,7 +407,7 @@ class Plan:
     def solve(self, y: torch.Tensor, I0: float, eta: float, iters: int, x: torch.Tensor | None = None,
               lo: float = 0.0, hi: float = math.inf, tol: float = 0.0, check_every: int = 1,
               average_tail: bool = False, stop_rule: str = "residual", tv_bound: float = 0.0,
-              tv_opts: dict | None = None, sync: bool = True):
+              tv_opts: dict | None = None, prox_lambda: float = 0.0, sync: bool = True):
         """Run up to ``iters`` extragradient iterations in place on ``x``
         (zeros if None).  stop_rule "residual" tests the relative change of the
         iterate, "average" the change of the running average of the last half
@@ -412,7 +428,8 @@ class Plan:
             hist = torch.empty((cap,) + tuple(self.shape_img), dtype=torch.float32, device=self.device)
         opts = _SolveOpts(float(lo), float(hi), float(tol), int(check_every), int(bool(average_tail)),
                           STOP_RULES[stop_rule], 0 if hist is None else hist.shape[0],
-                          None if hist is None else hist.data_ptr(), float(tv_bound), tv_options(tv_opts))
+                          None if hist is None else hist.data_ptr(), float(tv_bound), tv_options(tv_opts),
+                          float(prox_lambda))
         info = _SolveInfo()
         _check("exact_solve", load().exact_solve(self._h, _ptr(y), dt, float(I0), float(eta), int(iters),
                                                  ctypes.byref(opts), _ptr(x), ctypes.byref(info), _stream()))
@@ -570,7 +587,7 @@ class Batch:
             xs.append(x)
             arr[k] = _Job(p._h.value, jb.y.data_ptr(), dt, float(jb.I0), float(jb.eta), int(jb.iters),
                           _SolveOpts(float(jb.lo), float(jb.hi), float(jb.tol), int(jb.check_every), 0, 0, 0, None,
-                                     0.0, tv_options(None)),
+                                     0.0, tv_options(None), 0.0),
                           x.data_ptr(), ctypes.pointer(infos[k]))
         return arr, infos, xs
 

@@ -116,3 +116,27 @@ def test_solve_on_tv_ball_with_the_running_average_rule():
     xg = x.double().cpu().numpy()
     assert rel_l2(xg, ref.x) <= 1e-3
     assert info.avg_change == pytest.approx(ch[expect - 2], rel=1e-2)
+
+
+@pytest.mark.parametrize("nx,ny,lam", [(64, 64, 0.3), (37, 53, 1.5)])
+def test_tv_prox_parity(nx, ny, lam):
+    z = _noisy_phantom(nx, ny, 9)
+    ref, _, _ = T.prox_tv(z, lam, 60)
+    x = ex.tv_prox(torch.as_tensor(z, dtype=torch.float32, device=DEV), lam, 60)
+    assert rel_l2(x.double().cpu().numpy(), ref) <= 1e-5
+
+
+def test_proximal_variant_solve_parity():
+    geom = dict(beam=0, nx=40, ny=40, n_views=36, n_bins=59, angle_range=math.pi)
+    p = problem(geom, K=6, W=2, I0=1e4, seed=11)
+    nA, _ = oracle.norm_estimate(p["g_or"], 300, 1e-10)
+    eta = 1.0 / (4.0 * oracle.lipschitz(nA, p["S"], p["mu"], p["I0"], p["S"].shape[0] * p["g_or"].n_rays))
+    lam, iters = 0.05, 8
+    ref = T.solve_prox_tv(p["g_or"], p["S"], p["mu"], p["I0"], p["y"], eta, iters, lam, fgp_iters=30)
+    plan = ex.Plan(ex.Geometry(**geom), p["mu"], p["S"])
+    y = torch.as_tensor(p["y"], dtype=torch.float32, device=DEV)
+    x, info = plan.solve(y, p["I0"], eta, iters, prox_lambda=lam, tv_opts={"fgp_iters": 30})
+    assert info.status == 0 and info.iters_done == iters
+    assert rel_l2(x.double().cpu().numpy(), ref) <= 1e-4
+    with pytest.raises(RuntimeError):
+        plan.solve(y, p["I0"], eta, 2, prox_lambda=lam, tv_bound=10.0)
