@@ -105,10 +105,16 @@ def test_tv_ball_projection():
         assert float(((z - y) * (w - y)).sum()) <= 1e-4 * float(((z - y) ** 2).sum())
 
 
-def test_dykstra_matches_brute_force_qp_one_row():
+@pytest.mark.parametrize("z,tau", [
+    ([0.2, -0.3, 0.9, 1.4, 0.1, -0.5, 0.8, 0.3], 1.0),
+    # here plain alternating projections stop at a different point of X
+    ([1.2, 0.39, -0.44, -0.62, -0.16, 0.52, -0.71, 0.09], 0.8),
+    # and here Dykstra without the correction of the box step does
+    ([-0.93, -0.38, 0.23, -0.64, 0.2, 0.4, 0.34, -0.21], 1.5),
+])
+def test_dykstra_matches_brute_force_qp_one_row(z, tau):
     n = 8
-    z = np.array([0.2, -0.3, 0.9, 1.4, 0.1, -0.5, 0.8, 0.3])
-    tau = 1.0
+    z = np.array(z)
     opts = T.TvOptions(fgp_iters=400, tol_tv=1e-8, max_bisect=100, max_dykstra=400, tol_dykstra=1e-10)
     res = T.project_tv_box(z[None, :], tau, 0.0, np.inf, opts)
     # brute force: variables (x, s) with s_j >= |x_{j+1} - x_j|, sum s <= tau, x >= 0
@@ -124,7 +130,8 @@ def test_dykstra_matches_brute_force_qp_one_row():
     jac = lambda v: np.concatenate([v[:n] - z, np.zeros(m)])
     v0 = np.concatenate([np.clip(z, 0, None) * 0 + z.clip(0).mean(), np.zeros(m)])
     bounds = [(0, None)] * n + [(0, None)] * m
-    sol = minimize(fun, v0, jac=jac, constraints=[cons], bounds=bounds, method="trust-constr",
+    hess = lambda v: np.diag(np.concatenate([np.ones(n), np.zeros(m)]))
+    sol = minimize(fun, v0, jac=jac, hess=hess, constraints=[cons], bounds=bounds, method="trust-constr",
                    options={"gtol": 1e-12, "xtol": 1e-14, "maxiter": 20000})
     x_ref = sol.x[:n]
     assert T.tv(res.x) <= tau + 1e-5 and res.x.min() >= 0.0
