@@ -136,3 +136,32 @@ def test_dykstra_matches_brute_force_qp_one_row(z, tau):
     x_ref = sol.x[:n]
     assert T.tv(res.x) <= tau + 1e-5 and res.x.min() >= 0.0
     np.testing.assert_allclose(res.x[0], x_ref, atol=2e-4)
+
+
+def _small_problem():
+    import math
+    import oracle
+    from tests.cases import problem
+    geom = dict(beam=0, nx=16, ny=14, n_views=20, n_bins=23, angle_range=math.pi)
+    p = problem(geom, K=5, W=2, I0=1e4, seed=12)
+    nA, _ = oracle.norm_estimate(p["g_or"], 300, 1e-12)
+    eta = 1.0 / (4.0 * oracle.lipschitz(nA, p["S"], p["mu"], p["I0"], p["S"].shape[0] * p["g_or"].n_rays))
+    return oracle, p, eta
+
+
+def test_solve_tv_with_a_loose_ball_is_the_box_solve():
+    # a TV radius no iterate reaches: every projection is the box clamp
+    oracle, p, eta = _small_problem()
+    ref = oracle.solve(p["g_or"], p["S"], p["mu"], p["I0"], p["y"], eta, 15)
+    res = T.solve_tv(p["g_or"], p["S"], p["mu"], p["I0"], p["y"], eta, 15, tau=1e9)
+    np.testing.assert_allclose(res.x, ref.x, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(res.rel_res, ref.rel_res, rtol=1e-10)
+
+
+def test_solve_prox_tv_with_a_vanishing_lambda_is_the_unconstrained_solve():
+    # x = w + theta div p with |p| <= 1: the step moves x by at most 4 theta
+    oracle, p, eta = _small_problem()
+    ref = oracle.solve(p["g_or"], p["S"], p["mu"], p["I0"], p["y"], eta, 10, lo=-np.inf, hi=np.inf)
+    x = T.solve_prox_tv(p["g_or"], p["S"], p["mu"], p["I0"], p["y"], eta, 10, lam=1e-10, fgp_iters=5,
+                        lo=-np.inf, hi=np.inf)
+    np.testing.assert_allclose(x, ref.x, rtol=0, atol=1e-8)
