@@ -236,6 +236,7 @@ def c3():
     c = configs.C3
     p = problem(c["geometry"], K=c["K"], W=c["W"], I0=c["I0"], n_ellipses=c["n_ellipses"], seed=3, bf16=True)
     plan = _plan(c["geometry"], p["S"], p["mu"])
+    plan.autotune()  # as the benchmark does
     return c, p, plan
 
 
@@ -245,8 +246,13 @@ def test_c3_forward_adjoint_operator(c3):
     z = plan.forward(_gpu(x)).double().cpu().numpy()
     assert rel_l2(z, oracle.forward(p["g_or"], x)) <= 1e-5
     r = synth.random_sinogram(c["geometry"]["n_views"], c["geometry"]["n_bins"], seed=4, lo=-1, hi=1)
-    g = plan.adjoint(_gpu(r)).double().cpu().numpy()
-    assert rel_l2(g, oracle.adjoint(p["g_or"], r)) <= 1e-5
+    ref = oracle.adjoint(p["g_or"], r)
+    tuned = plan.tuning["adj_split"]
+    for s in (tuned, 1, 8):  # the autotuned split, and the extremes
+        plan.set_tuning(s)
+        g = plan.adjoint(_gpu(r)).double().cpu().numpy()
+        assert rel_l2(g, ref) <= 1e-5
+    plan.set_tuning(tuned)
     F = plan.operator(_gpu(0.5 * x), _gpu(p["y"], torch.bfloat16), p["I0"]).double().cpu().numpy()
     assert rel_l2(F, oracle.operator(p["g_or"], 0.5 * x, p["S"], p["mu"], p["I0"], p["y"])) <= 1e-5
 
