@@ -17,7 +17,8 @@
 // All of it runs as one persistent cooperative launch: every CTA owns a
 // grid-stride share of the pixels, phases are separated by a grid barrier
 // (bounded spin: on a timeout the kernel records EXACT_ERR_TIMEOUT and
-// returns), and every decision (bisection branch, stop tests) is taken by all
+// returns; the dual steps run kTvK at a time between barriers, see
+// fgp_block), and every decision (bisection branch, stop tests) is taken by all
 // CTAs on the same FP64 sum, reduced in a fixed order, so the run is
 // deterministic.  Pixel arrays are FP32; data rewritten during the launch is
 // read through L2 (__ldcg), since L1 is not coherent across CTAs.
@@ -156,78 +157,102 @@ __device__ __forceinline__ float prox_x(const float *w, const float *rx, const f
     return fmaf(theta, dv, __ldcg(w + q));
 }
 
-// One dual step of the fast gradient projection method over the image, tile
-// by tile: a kTvTH x kTvTW tile with its one-pixel halo of w, rx, ry is staged
-// in shared memory (coalesced), x = w + theta div r is formed on the tile and
-// one extra row and column, and each pixel updates (p, r) from grad x.
-constexpr int kTvTW = 32, kTvTH = kTvThreads / kTvTW;
+// Up to kTvK dual steps of the fast gradient projection method between two
+// grid barriers (temporal blocking).  A CTA stages a kTvT x kTvT tile of the
+// image with a halo of kTvK pixels (w, r and p) in shared memory and runs the
+// steps on the whole staged region: every step needs r at distance one, so
+// the garbage that enters from the region's edge moves in by one pixel per
+// step and the tile itself stays exact; the tile's new p and r are then
+// written to the second buffers.  Per pixel the arithmetic is that of one
+// step over the whole image, so the result does not depend on kTvK.
+constexpr int kTvT = 32, kTvK = 8, kTvR = kTvT + 2 * kTvK;
 
 struct TvSmem {
-    float w[kTvTH + 2][kTvTW + 2], rx[kTvTH + 2][kTvTW + 2], ry[kTvTH + 2][kTvTW + 2];
-    float x[kTvTH + 1][kTvTW + 1];
+    float w[kTvR][kTvR], rx[kTvR][kTvR], ry[kTvR][kTvR], px[kTvR][kTvR], py[kTvR][kTvR], x[kTvR][kTvR];
 };
 
-__device__ void fgp_step(const TvArgs &a, TvSmem &sm, const float *rx, const float *ry, const float *px,
-                         const float *py, float *px2, float *py2, float *rx2, float *ry2, float theta, float step,
-                         float beta)
+__device__ void fgp_block(const TvArgs &a, TvSmem &sm, const float *rx, const float *ry, const float *px,
+                          const float *py, float *px2, float *py2, float *rx2, float *ry2, float theta, float step,
+                          double &t, int nsteps)
 {
     const int nx = a.nx, ny = a.ny;
-    const int tiles_x = (nx + kTvTW - 1) / kTvTW, tiles = tiles_x * ((ny + kTvTH - 1) / kTvTH);
+    const int tiles_x = (nx + kTvT - 1) / kTvT, tiles = tiles_x * ((ny + kTvT - 1) / kTvT);
+    const double t_start = t;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int i0 = (tile / tiles_x) * kTvTH, j0 = (tile % tiles_x) * kTvTW;
-        // stage rows i0-1 .. i0+TH, columns j0-1 .. j0+TW (zeros outside the image)
-        for (int e = threadIdx.x; e < (kTvTH + 2) * (kTvTW + 2); e += kTvThreads) {
-            const int li = e / (kTvTW + 2), lj = e % (kTvTW + 2);
-            const int gi = i0 - 1 + li, gj = j0 - 1 + lj;
-            float vw = 0.0f, vx = 0.0f, vy = 0.0f;
+        const int i0 = (tile / tiles_x) * kTvT - kTvK, j0 = (tile % tiles_x) * kTvT - kTvK;  // region origin
+        for (int e = threadIdx.x; e < kTvR * kTvR; e += kTvThreads) {
+            const int li = e / kTvR, lj = e % kTvR, gi = i0 + li, gj = j0 + lj;
+            float vw = 0.0f, vrx = 0.0f, vry = 0.0f, vpx = 0.0f, vpy = 0.0f;
             if (gi >= 0 && gi < ny && gj >= 0 && gj < nx) {
                 const long long q = (long long)gi * nx + gj;
                 vw = __ldcg(a.w + q);
-                vx = __ldcg(rx + q);
-                vy = __ldcg(ry + q);
+                vrx = __ldcg(rx + q);
+                vry = __ldcg(ry + q);
+                vpx = __ldcg(px + q);
+                vpy = __ldcg(py + q);
             }
             sm.w[li][lj] = vw;
-            sm.rx[li][lj] = vx;
-            sm.ry[li][lj] = vy;
+            sm.rx[li][lj] = vrx;
+            sm.ry[li][lj] = vry;
+            sm.px[li][lj] = vpx;
+            sm.py[li][lj] = vpy;
         }
         __syncthreads();
-        // x on tile rows 0 .. TH and columns 0 .. TW (the extra row / column
-        // feed the forward differences of the last ones)
-        for (int e = threadIdx.x; e < (kTvTH + 1) * (kTvTW + 1); e += kTvThreads) {
-            const int li = e / (kTvTW + 1), lj = e % (kTvTW + 1);
-            const int gi = i0 + li, gj = j0 + lj;
-            float dv = 0.0f;
-            if (gj < nx - 1) dv += sm.rx[li + 1][lj + 1];
-            if (gj > 0) dv -= sm.rx[li + 1][lj];
-            if (gi < ny - 1) dv += sm.ry[li + 1][lj + 1];
-            if (gi > 0) dv -= sm.ry[li][lj + 1];
-            sm.x[li][lj] = fmaf(theta, dv, sm.w[li + 1][lj + 1]);
+        double tt = t_start;
+        for (int k = 0; k < nsteps; ++k) {
+            const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tt * tt));
+            const float beta = (float)((tt - 1.0) / tn);
+            tt = tn;
+            // x = w + theta div r (region positions without a neighbour take 0:
+            // they are in the garbage ring or outside the image, unused)
+            for (int e = threadIdx.x; e < kTvR * kTvR; e += kTvThreads) {
+                const int li = e / kTvR, lj = e % kTvR, gi = i0 + li, gj = j0 + lj;
+                float dv = 0.0f;
+                if (gj < nx - 1) dv += sm.rx[li][lj];
+                if (gj > 0 && lj > 0) dv -= sm.rx[li][lj - 1];
+                if (gi < ny - 1) dv += sm.ry[li][lj];
+                if (gi > 0 && li > 0) dv -= sm.ry[li - 1][lj];
+                sm.x[li][lj] = fmaf(theta, dv, sm.w[li][lj]);
+            }
+            __syncthreads();
+            // (p, r) update from grad x, in place (each position reads only its own p, r)
+            for (int e = threadIdx.x; e < kTvR * kTvR; e += kTvThreads) {
+                const int li = e / kTvR, lj = e % kTvR, gi = i0 + li, gj = j0 + lj;
+                const float x0 = sm.x[li][lj];
+                const float gx = (gj < nx - 1 && lj + 1 < kTvR) ? sm.x[li][lj + 1] - x0 : 0.0f;
+                const float gy = (gi < ny - 1 && li + 1 < kTvR) ? sm.x[li + 1][lj] - x0 : 0.0f;
+                const float qx = fmaf(step, gx, sm.rx[li][lj]);
+                const float qy = fmaf(step, gy, sm.ry[li][lj]);
+                const float nrm = fmaxf(1.0f, sqrtf(qx * qx + qy * qy));
+                const float nx_ = qx / nrm, ny_ = qy / nrm;
+                sm.rx[li][lj] = fmaf(beta, nx_ - sm.px[li][lj], nx_);
+                sm.ry[li][lj] = fmaf(beta, ny_ - sm.py[li][lj], ny_);
+                sm.px[li][lj] = nx_;
+                sm.py[li][lj] = ny_;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        const int li = threadIdx.x / kTvTW, lj = threadIdx.x % kTvTW;
-        const int gi = i0 + li, gj = j0 + lj;
-        if (gi < ny && gj < nx) {
-            const long long q = (long long)gi * nx + gj;
-            const float x0 = sm.x[li][lj];
-            const float gx = gj < nx - 1 ? sm.x[li][lj + 1] - x0 : 0.0f;
-            const float gy = gi < ny - 1 ? sm.x[li + 1][lj] - x0 : 0.0f;
-            const float qx = fmaf(step, gx, sm.rx[li + 1][lj + 1]);
-            const float qy = fmaf(step, gy, sm.ry[li + 1][lj + 1]);
-            const float nrm = fmaxf(1.0f, sqrtf(qx * qx + qy * qy));
-            const float nx_ = qx / nrm, ny_ = qy / nrm;
-            px2[q] = nx_;
-            py2[q] = ny_;
-            rx2[q] = fmaf(beta, nx_ - __ldcg(px + q), nx_);
-            ry2[q] = fmaf(beta, ny_ - __ldcg(py + q), ny_);
+        // the tile (exact after nsteps <= kTvK steps) to the second buffers
+        for (int e = threadIdx.x; e < kTvT * kTvT; e += kTvThreads) {
+            const int li = kTvK + e / kTvT, lj = kTvK + e % kTvT, gi = i0 + li, gj = j0 + lj;
+            if (gi < ny && gj < nx) {
+                const long long q = (long long)gi * nx + gj;
+                px2[q] = sm.px[li][lj];
+                py2[q] = sm.py[li][lj];
+                rx2[q] = sm.rx[li][lj];
+                ry2[q] = sm.ry[li][lj];
+            }
         }
         __syncthreads();
     }
+    for (int k = 0; k < nsteps; ++k) t = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
 }
 
-__global__ void __launch_bounds__(kTvThreads) k_tv_project(TvArgs a)
+__global__ void __launch_bounds__(kTvThreads, 2) k_tv_project(TvArgs a)
 {
     if (a.done && ld_volatile_i32(a.done)) return;
-    __shared__ TvSmem sm;
+    extern __shared__ __align__(16) unsigned char tv_smem[];
+    TvSmem &sm = *reinterpret_cast<TvSmem *>(tv_smem);
     const long long stride = (long long)gridDim.x * kTvThreads;
     const long long first = (long long)blockIdx.x * kTvThreads + threadIdx.x;
     const int nx = a.nx, ny = a.ny;
@@ -269,17 +294,15 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_project(TvArgs a)
                 }
                 if (!grid_barrier(a.bar, a.err, a.done)) return;
                 double t = 1.0;
-                for (int it = 0; it < a.fgp_iters; ++it) {
-                    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-                    const float beta = (float)((t - 1.0) / tn);
-                    fgp_step(a, sm, rx, ry, px, py, px2, py2, rx2, ry2, theta, step, beta);
+                for (int it = 0; it < a.fgp_iters; it += kTvK) {
+                    const int ns = a.fgp_iters - it < kTvK ? a.fgp_iters - it : kTvK;
+                    fgp_block(a, sm, rx, ry, px, py, px2, py2, rx2, ry2, theta, step, t, ns);
                     if (!grid_barrier(a.bar, a.err, a.done)) return;
                     float *tp;
                     tp = px; px = px2; px2 = tp;
                     tp = py; py = py2; py2 = tp;
                     tp = rx; rx = rx2; rx2 = tp;
                     tp = ry; ry = ry2; ry2 = tp;
-                    t = tn;
                 }
                 for (long long q = first; q < a.d; q += stride)
                     a.xt[q] = prox_x(a.w, px, py, theta, (int)(q / nx), (int)(q % nx), nx, ny);
@@ -377,7 +400,10 @@ int tv_grid(long long d)
     if (!g_tv_grid[dev]) {
         int sms = 0, per = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tv_project, kTvThreads, 0) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_tv_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TvSmem)) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tv_project, kTvThreads, sizeof(TvSmem)) !=
+                cudaSuccess)
             return 0;
         if (per < 1) return 0;
         g_tv_grid[dev] = sms * (per < 4 ? per : 4);
@@ -440,7 +466,8 @@ cudaError_t launch_tv_project(const TvLaunch &L, cudaStream_t s)
     cudaError_t e = cudaMemsetAsync(tail->bar, 0, sizeof(tail->bar), s);
     if (e != cudaSuccess) return e;
     void *args[] = {&a};
-    return cudaLaunchCooperativeKernel((const void *)k_tv_project, dim3(L.grid), dim3(kTvThreads), args, 0, s);
+    return cudaLaunchCooperativeKernel((const void *)k_tv_project, dim3(L.grid), dim3(kTvThreads), args,
+                                       sizeof(TvSmem), s);
 }
 
 }  // namespace exact
