@@ -59,6 +59,7 @@ def parse_args(argv=None):
     p.add_argument("--no-tv", action="store_true", help="skip the TV-ball feasible-set measurement")
     p.add_argument("--no-gaussian", action="store_true", help="skip the Gaussian-model (Fig. 6) measurement")
     p.add_argument("--serve-jobs", type=int, default=32)
+    p.add_argument("--serve-round-iters", type=int, default=20, help="iterations per server round")
     p.add_argument("--serve-loads", default="0.8,1.5",
                    help="arrival rates as fractions of the measured sequential capacity")
     return p.parse_args(argv)
@@ -261,7 +262,7 @@ def make_counts(ex, torch, spec, dev, rank=0):
     return plan, y, mu, S, xs
 
 
-def run_served(ex, torch, dev, n_jobs: int, loads, rank: int):
+def run_served(ex, torch, dev, n_jobs: int, loads, rank: int, round_iters: int = 20):
     """A Poisson stream of reconstruction requests (image sizes 128..512,
     90..720 views, parallel or fan beam, 1..4 windows, 16..64 energies,
     tolerance 1e-3) served (a) by the continuous-batching Server and (b) one at
@@ -300,7 +301,7 @@ def run_served(ex, torch, dev, n_jobs: int, loads, rank: int):
         for r in reqs:
             t += float(rng.exponential(1.0 / rate))
             r.arrival = t
-        server = Server(budget_bytes=configs.C5["budget_bytes"], max_slots=64, round_iters=20)
+        server = Server(budget_bytes=configs.C5["budget_bytes"], max_slots=64, round_iters=round_iters)
         served = summarise(server.run(reqs, realtime=True))
         served["rounds"] = server.rounds
         server.close()
@@ -310,7 +311,7 @@ def run_served(ex, torch, dev, n_jobs: int, loads, rank: int):
                        "p99_latency_ratio": plain["p99_latency_s"] / served["p99_latency_s"]})
     return {"requests": n_jobs, "sequential_capacity_per_s": cap,
             "workload": "Poisson stream; 128..512^2, 90..720 views, parallel/fan 50/50, 1..4 windows, 16..64 "
-                        "energies, tol 1e-3, HBM budget 150 GB, 20 iterations per round",
+                        f"energies, tol 1e-3, HBM budget 150 GB, {round_iters} iterations per round",
             "loads": points}
 
 
@@ -688,7 +689,8 @@ def run_exact(args):
         line["batched"] = run_batched(ex, torch, dev, args.batch_jobs, args.batch_iters or configs.C4["iters"], rank)
     if not args.no_served:
         line["served"] = run_served(ex, torch, dev, args.serve_jobs,
-                                    [float(v) for v in args.serve_loads.split(",") if v], rank)
+                                    [float(v) for v in args.serve_loads.split(",") if v], rank,
+                                    args.serve_round_iters)
     if not args.no_tv:
         line["tv"] = run_tv(ex, torch, dev, rank)
     if not args.no_gaussian:
