@@ -44,7 +44,6 @@ struct __align__(128) BatchSmem {
         AdjSmem<kBG> adj;
     } u;
     uint64_t bar[kFStages];
-    int prefix[5 * kMaxBatch + 1];
     unsigned long long item;
     int ok;
     int go;
@@ -93,7 +92,7 @@ __device__ void batch_reduce(const BatchJob &J, int iter, double *scratch)
     }
 }
 
-__global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(kBatchThreads, 6) k_batch(const BatchJob *__restrict__ jobs, int n_jobs,
                                                          const int *__restrict__ prefix_g, int rounds,
                                                          unsigned long long *next, unsigned *done_items,
                                                          int *abort_flag)
@@ -101,13 +100,12 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
     __shared__ BatchSmem sm;
     const int t = threadIdx.x;
     const int nseg = 5 * n_jobs;
-    for (int i = t; i <= nseg; i += kBatchThreads) sm.prefix[i] = prefix_g[i];
     if (t == 0) {
         for (int q = 0; q < kFStages; ++q) mbar_init(&sm.bar[q]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const unsigned long long per_round = (unsigned long long)sm.prefix[nseg];
+    const unsigned long long per_round = (unsigned long long)__ldg(prefix_g + nseg);
     const unsigned long long total = per_round * (unsigned long long)rounds;
     uint32_t fphase = 0u;  // staging-barrier parities of the forward items
 
@@ -122,11 +120,11 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
         int lo = 0, hi = nseg - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (sm.prefix[mid] <= rem) lo = mid;
+            if (__ldg(prefix_g + mid) <= rem) lo = mid;
             else hi = mid - 1;
         }
         const int phase = lo / n_jobs, j = lo - phase * n_jobs;
-        const int local = rem - sm.prefix[lo];
+        const int local = rem - __ldg(prefix_g + lo);
         const BatchJob &J = jobs[j];
 
         if (t == 0) {
