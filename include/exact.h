@@ -222,8 +222,9 @@ exact_status exact_plan_get_tuning(exact_plan_t plan, exact_tuning *out);
 exact_status exact_plan_set_tuning(exact_plan_t plan, const exact_tuning *tuning);
 
 /* Autotuner: times the adjoint of this plan's geometry on the device for
- * adj_split in {1, 2, 3, 4, 6, 8} (median of 5 launches each) and keeps the
- * fastest, a larger split only when it is more than 3% faster.  The choice is
+ * adj_split in {1, 2, 3, 4, 6, 8} (9 rounds after a warm-up round, one launch
+ * of each value per round; median per value) and keeps the fastest, a larger
+ * split only when it is more than 1% faster.  The choice is
  * cached per geometry shape (beam, nx, ny, n_views, n_bins) for the life of
  * the process: later plans of a tuned shape take it without timing unless
  * force != 0.  out may be NULL.  Uses the plan's workspace as scratch;

@@ -801,27 +801,31 @@ exact_status exact_plan_autotune(exact_plan_t plan, int force, exact_tuning *out
         return EXACT_ERR_CUDA;
     }
     const bool fan = P.g.beam == 1;
-    int best = 1;
-    float best_ms = INFINITY;
+    // candidates are timed round-robin (one launch each per round, after a
+    // warm-up round) so that clock drift spreads over all of them
+    constexpr int kCands = (int)(sizeof(kSplitCandidates) / sizeof(kSplitCandidates[0]));
+    constexpr int kRounds = 9;
+    float ms[kCands][kRounds];
     cudaError_t e = cudaSuccess;
-    for (int cand : kSplitCandidates) {
-        a.nsplit = cand;
-        constexpr int kReps = 5;
-        float ms[kReps];
-        e = launch_adjoint(a, ADJ_PLAIN, fan, s);  // warm
-        for (int r = 0; r < kReps && e == cudaSuccess; ++r) {
+    for (int r = -1; r < kRounds && e == cudaSuccess; ++r)
+        for (int c = 0; c < kCands && e == cudaSuccess; ++c) {
+            a.nsplit = kSplitCandidates[c];
             e = cudaEventRecord(e0, s);
             if (e == cudaSuccess) e = launch_adjoint(a, ADJ_PLAIN, fan, s);
             if (e == cudaSuccess) e = cudaEventRecord(e1, s);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[r], e0, e1);
+            float t = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+            if (r >= 0) ms[c][r] = t;
         }
-        if (e != cudaSuccess) break;
-        std::sort(ms, ms + kReps);
-        // prefer fewer CTAs per tile unless a larger split is clearly faster
-        if (ms[kReps / 2] < 0.97f * best_ms) {
-            best_ms = ms[kReps / 2];
-            best = cand;
+    int best = 1;
+    float best_ms = INFINITY;
+    for (int c = 0; c < kCands && e == cudaSuccess; ++c) {
+        std::sort(ms[c], ms[c] + kRounds);
+        // the fastest median; a larger split must beat a smaller one by 1%
+        if (ms[c][kRounds / 2] < 0.99f * best_ms) {
+            best_ms = ms[c][kRounds / 2];
+            best = kSplitCandidates[c];
         }
     }
     cudaEventDestroy(e0);
