@@ -55,7 +55,7 @@ typedef enum {
     EXACT_ERR_OOM = 3,         /* device or pinned memory could not be allocated */
     EXACT_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
     EXACT_ERR_NONFINITE = 5,   /* a NaN/Inf residual norm stopped a solve */
-    EXACT_ERR_UNSUPPORTED = 6, /* valid input outside what this build handles */
+    EXACT_ERR_UNSUPPORTED = 6, /* valid input outside what the library supports */
     EXACT_ERR_NO_WORKSPACE = 7 /* the call needs a bound workspace */
 } exact_status;
 
