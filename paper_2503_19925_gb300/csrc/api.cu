@@ -328,6 +328,15 @@ ViewRec make_view(const exact_geometry &g, int v, int xb0, int xb1, int yb0, int
     return r;
 }
 
+// The per-tile arrival counts of the adjoint's view split are zero between
+// launches (the last CTA of a tile resets its count); a launch cut short (a
+// timed-out batch) could leave some set, so every call that launches the
+// adjoint clears them first.
+cudaError_t reset_split_counts(const Plan &P, cudaStream_t s)
+{
+    return cudaMemsetAsync(P.split_count, 0, sizeof(int) * (size_t)adjoint_blocks(P.g.nx, P.g.ny), s);
+}
+
 exact_status check_plan(exact_plan_t p, bool need_ws)
 {
     if (!p) return EXACT_ERR_INVALID_ARG;
@@ -781,6 +790,7 @@ exact_status exact_plan_autotune(exact_plan_t plan, int force, exact_tuning *out
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     EXACT_TRY(cudaMemsetAsync(P.r, 0, sizeof(float) * (size_t)P.n, s));
+    EXACT_TRY(reset_split_counts(P, s));
     AdjArgs a;
     memset(&a, 0, sizeof(a));
     a.rays = P.rays_f;
@@ -884,6 +894,7 @@ exact_status exact_adjoint(exact_plan_t plan, const float *r, float *g, exact_st
     a.delta = P.ray_delta;
     a.scale = 1.0f;
     a.out = g;
+    EXACT_TRY(reset_split_counts(P, reinterpret_cast<cudaStream_t>(stream)));
     EXACT_TRY(launch_adjoint(a, ADJ_PLAIN, P.g.beam == 1, reinterpret_cast<cudaStream_t>(stream)));
     return EXACT_OK;
 }
@@ -932,6 +943,7 @@ exact_status exact_operator(exact_plan_t plan, const float *x, const void *y, ex
     a.r = P.r;
     a.scale = (float)(1.0 / ((double)P.W * (double)P.n));
     a.out = F;
+    EXACT_TRY(reset_split_counts(P, s));
     EXACT_TRY(launch_adjoint(a, ADJ_PLAIN, P.g.beam == 1, s));
     return EXACT_OK;
 }
@@ -970,6 +982,7 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     const int nb = adjoint_blocks(P.g.nx, P.g.ny);
 
     EXACT_TRY(launch_reset_state(P.state, s));
+    EXACT_TRY(reset_split_counts(P, s));
     EXACT_TRY(launch_collapse(y, y_dtype, P.W, P.n, P.Y, s));
     EXACT_TRY(launch_pack(x, P.xr[0], P.xc[0], P.g.nx, P.g.ny, P.ldr(), P.ldc(), lo, hi, true, s));
     EXACT_TRY(cudaMemsetAsync(P.xr[1], 0, sizeof(float) * (size_t)(P.g.ny * P.ldr()), s));
@@ -1195,6 +1208,7 @@ exact_status exact_norm_estimate_f32(exact_plan_t plan, int max_iters, double rt
     a.scale = 1.0f;
     a.out = P.w32;
     a.state = P.state;
+    EXACT_TRY(reset_split_counts(P, s));
     const int chunk = 8;
     for (int it0 = 0; it0 < max_iters; it0 += chunk) {
         const int it1 = it0 + chunk < max_iters ? it0 + chunk : max_iters;
@@ -1530,6 +1544,7 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
         const exact_job &Jb = jobs[j];
         Plan &P = *reinterpret_cast<Plan *>(Jb.plan);
         EXACT_TRY(launch_reset_state(P.state, s));
+        EXACT_TRY(reset_split_counts(P, s));
         EXACT_TRY(launch_collapse(Jb.y, Jb.y_dtype, P.W, P.n, P.Y, s));
         EXACT_TRY(launch_pack(Jb.x, P.xr[0], P.xc[0], P.g.nx, P.g.ny, P.ldr(), P.ldc(), (float)Jb.opts.lo,
                               (float)Jb.opts.hi, true, s));
