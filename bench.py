@@ -405,7 +405,7 @@ def run_tv(ex, torch, dev, rank: int):
     normA, _ = plan.norm_estimate(max_iters=200, rtol=1e-9)
     eta = plan.recommended_eta(spec["I0"], normA)
     tau3 = tv_norm_np(xs3)
-    max_iters = 3000
+    max_iters = 20000
     a = ev()
     x, sinfo = plan.solve(y, spec["I0"], eta, max_iters, tv_bound=tau3, stop_rule="average", tol=1e-5)
     b = ev()
