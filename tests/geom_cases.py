@@ -17,4 +17,8 @@ def tiny_geometries():
                  bin_pitch=1.2, det_offset=-0.4, src_to_center=11.0, src_to_det=19.0),
         Geometry(beam=1, nx=16, ny=16, n_views=6, n_bins=31, angle0=0.7, angle_range=2 * np.pi,
                  bin_pitch=1.0, src_to_center=14.0, src_to_det=21.0),
+        # views at multiples of 45 degrees: driving-axis ties (|dir_x| = |dir_y| up to rounding)
+        Geometry(beam=0, nx=8, ny=6, n_views=4, n_bins=13, angle_range=np.pi),
+        Geometry(beam=1, nx=10, ny=10, n_views=8, n_bins=17, angle_range=2 * np.pi, bin_pitch=1.5,
+                 src_to_center=25.0, src_to_det=37.5),
     ]

@@ -268,6 +268,31 @@ def test_c3_solve_first_iterations_and_norm(c3):
     assert rel_l2(x.double().cpu().numpy(), refx.x) <= 1e-4
 
 
+# ---- the largest request of the serving stream: 1024^2 image, 1440 views ----
+
+def test_max_size_forward_adjoint_operator():
+    """1024^2 fan beam, 1440 views x 1449 bins (the top of the serving mix):
+    A x, A^T r (autotuned split and no split) and F(x) against the oracle."""
+    geom = dict(beam=1, nx=1024, ny=1024, n_views=1440, n_bins=1449, angle_range=2 * math.pi, bin_pitch=1.5,
+                src_to_center=2000.0, src_to_det=3000.0)
+    p = problem(geom, K=16, W=2, I0=1e4, seed=11, bf16=True)
+    plan = _plan(geom, p["S"], p["mu"])
+    plan.autotune()
+    x = p["xs"]
+    z = plan.forward(_gpu(x)).double().cpu().numpy()
+    assert rel_l2(z, oracle.forward(p["g_or"], x)) <= 1e-5
+    r = synth.random_sinogram(geom["n_views"], geom["n_bins"], seed=12, lo=-1, hi=1)
+    ref = oracle.adjoint(p["g_or"], r)
+    tuned = plan.tuning["adj_split"]
+    for s in sorted({tuned, 1}):
+        plan.set_tuning(s)
+        g = plan.adjoint(_gpu(r)).double().cpu().numpy()
+        assert rel_l2(g, ref) <= 1e-5
+    plan.set_tuning(tuned)
+    F = plan.operator(_gpu(0.5 * x), _gpu(p["y"], torch.bfloat16), p["I0"]).double().cpu().numpy()
+    assert rel_l2(F, oracle.operator(p["g_or"], 0.5 * x, p["S"], p["mu"], p["I0"], p["y"])) <= 1e-5
+
+
 @pytest.mark.parametrize("gi", [0, 2])
 def test_known_background_operator_and_solve(gi):
     """Appendix A.1: known materials enter through their projections."""
