@@ -177,7 +177,21 @@ __device__ void fgp_block(const TvArgs &a, TvSmem &sm, const float *rx, const fl
 {
     const int nx = a.nx, ny = a.ny;
     const int tiles_x = (nx + kTvT - 1) / kTvT, tiles = tiles_x * ((ny + kTvT - 1) / kTvT);
-    const double t_start = t;
+    // momentum of the fast gradient method, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
+    // and beta_k = (t_k - 1) / t_{k+1}, in FP64 by one thread (FP64 runs at a
+    // small fraction of the FP32 rate) and shared with the CTA
+    __shared__ float s_beta[kTvK];
+    __shared__ double s_t;
+    if (threadIdx.x == 0) {
+        double tt = t;
+        for (int k = 0; k < nsteps; ++k) {
+            const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tt * tt));
+            s_beta[k] = (float)((tt - 1.0) / tn);
+            tt = tn;
+        }
+        s_t = tt;
+    }
+    __syncthreads();
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int i0 = (tile / tiles_x) * kTvT - kTvK, j0 = (tile % tiles_x) * kTvT - kTvK;  // region origin
         for (int e = threadIdx.x; e < kTvR * kTvR; e += kTvThreads) {
@@ -198,11 +212,8 @@ __device__ void fgp_block(const TvArgs &a, TvSmem &sm, const float *rx, const fl
             sm.py[li][lj] = vpy;
         }
         __syncthreads();
-        double tt = t_start;
         for (int k = 0; k < nsteps; ++k) {
-            const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tt * tt));
-            const float beta = (float)((tt - 1.0) / tn);
-            tt = tn;
+            const float beta = s_beta[k];
             // x = w + theta div r (region positions without a neighbour take 0:
             // they are in the garbage ring or outside the image, unused)
             for (int e = threadIdx.x; e < kTvR * kTvR; e += kTvThreads) {
@@ -245,7 +256,8 @@ __device__ void fgp_block(const TvArgs &a, TvSmem &sm, const float *rx, const fl
         }
         __syncthreads();
     }
-    for (int k = 0; k < nsteps; ++k) t = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    t = s_t;
+    __syncthreads();  // s_t and s_beta are rewritten by the next call
 }
 
 __global__ void __launch_bounds__(kTvThreads, 2) k_tv_project(TvArgs a)
