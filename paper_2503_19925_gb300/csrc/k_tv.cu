@@ -31,7 +31,7 @@ namespace exact {
 
 namespace {
 
-constexpr int kTvThreads = 256;
+constexpr int kTvThreads = 384;  // 8 rows x 48 columns of a dual-step region
 constexpr long long kTvBarrierSpins = 1LL << 22;
 
 struct TvArgs {
@@ -106,13 +106,19 @@ __device__ bool grid_barrier(unsigned *bar, int *err, int *done)
     return s_ok != 0;
 }
 
-// Fixed-order CTA sum of one double per thread (result valid in every thread).
+// Fixed-order CTA sum of one double per thread (result valid in every thread):
+// the entries past the largest power of two kTvPow2 are folded in first.
+constexpr int kTvPow2 = 256;
+static_assert(kTvThreads >= kTvPow2 && kTvThreads <= 2 * kTvPow2, "one fold step");
+
 __device__ double block_sum(double v)
 {
     __shared__ double s[kTvThreads];
     s[threadIdx.x] = v;
     __syncthreads();
-    for (int h = kTvThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < kTvThreads - kTvPow2) s[threadIdx.x] += s[threadIdx.x + kTvPow2];
+    __syncthreads();
+    for (int h = kTvPow2 / 2; h > 0; h >>= 1) {
         if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
         __syncthreads();
     }
@@ -132,6 +138,17 @@ __device__ double grid_sum(const TvArgs &a, double v, int slot, bool &ok)
     for (int i = threadIdx.x; i < (int)gridDim.x; i += kTvThreads)
         s += __ldcg(a.part + (long long)slot * gridDim.x + i);
     return block_sum(s);
+}
+
+// Row and column of flat pixel index q (32-bit division while q fits).
+__device__ __forceinline__ int tv_row(long long q, int nx)
+{
+    return q <= 0x7fffffffLL ? (int)q / nx : (int)(q / nx);
+}
+
+__device__ __forceinline__ int tv_col(long long q, int nx)
+{
+    return q <= 0x7fffffffLL ? (int)q % nx : (int)(q % nx);
 }
 
 // Isotropic TV term of pixel (i, j) of image v.
@@ -159,20 +176,39 @@ __device__ __forceinline__ float prox_x(const float *w, const float *rx, const f
 
 // Up to kTvK dual steps of the fast gradient projection method between two
 // grid barriers (temporal blocking).  A CTA stages a kTvT x kTvT tile of the
-// image with a halo of kTvK pixels (w, r and p) in shared memory and runs the
-// steps on the whole staged region: every step needs r at distance one, so
-// the garbage that enters from the region's edge moves in by one pixel per
-// step and the tile itself stays exact; the tile's new p and r are then
-// written to the second buffers.  Per pixel the arithmetic is that of one
-// step over the whole image, so the result does not depend on kTvK.
+// image with a halo of kTvK pixels (w, r and p) and runs the steps on the whole
+// staged region: every step needs r at distance one, so the garbage that
+// enters from the region's edge moves in by one pixel per step and the tile
+// itself stays exact; the tile's new p and r are then written to the second
+// buffers.  Per pixel the arithmetic is that of one step over the whole image,
+// so the result does not depend on kTvK.
+//
+// Thread (tr, c) of the CTA owns region column c and rows tr + kTvRows m
+// (m < kTvM); its w, r, p and x stay in registers, and only r and x, which
+// the neighbours read, go through shared memory.  The boundary rule needs no
+// branch in the divergence: r_x is zero at the last image column and r_y at
+// the last row (their gradient components are zero there, and the duals start
+// at zero), and every position outside the image is staged as zero with its
+// gradient components masked, so the terms the rule drops are exact zeros.
+// The shared arrays are flat with row stride kTvR (= 16 mod 32 words, no bank
+// conflicts across the two rows a warp touches); r has one leading pad row and
+// column, x one trailing: region-edge reads land on the pad or on another
+// edge position, and feed only the garbage ring.
 constexpr int kTvT = 32, kTvK = 8, kTvR = kTvT + 2 * kTvK;
+constexpr int kTvRows = kTvThreads / kTvR;  // rows of the region per pass of the CTA
+constexpr int kTvM = kTvR / kTvRows;        // region positions per thread
+static_assert(kTvRows * kTvR == kTvThreads && kTvM * kTvRows == kTvR, "threads tile the region");
 
 struct TvSmem {
-    float w[kTvR][kTvR], rx[kTvR][kTvR], ry[kTvR][kTvR], px[kTvR][kTvR], py[kTvR][kTvR], x[kTvR][kTvR];
+    float rx[(kTvR + 1) * kTvR + 1];  // r_x at (li, lj): [(li + 1) kTvR + lj + 1], li, lj >= -1
+    float ry[(kTvR + 1) * kTvR + 1];
+    float x[(kTvR + 1) * kTvR + 1];   // x at (li, lj): [li kTvR + lj], li, lj <= kTvR
 };
 
-__device__ void fgp_block(const TvArgs &a, TvSmem &sm, const float *rx, const float *ry, const float *px,
-                          const float *py, float *px2, float *py2, float *rx2, float *ry2, float theta, float step,
+__device__ __forceinline__ int tv_ri(int li, int lj) { return (li + 1) * kTvR + lj + 1; }
+
+__device__ void fgp_block(const TvArgs &a, TvSmem &sm, const float *rxg, const float *ryg, const float *pxg,
+                          const float *pyg, float *px2, float *py2, float *rx2, float *ry2, float theta, float step,
                           double &t, int nsteps)
 {
     const int nx = a.nx, ny = a.ny;
@@ -192,69 +228,82 @@ __device__ void fgp_block(const TvArgs &a, TvSmem &sm, const float *rx, const fl
         s_t = tt;
     }
     __syncthreads();
+    const int tr = threadIdx.x / kTvR, lj = threadIdx.x - tr * kTvR;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int i0 = (tile / tiles_x) * kTvT - kTvK, j0 = (tile % tiles_x) * kTvT - kTvK;  // region origin
-        for (int e = threadIdx.x; e < kTvR * kTvR; e += kTvThreads) {
-            const int li = e / kTvR, lj = e % kTvR, gi = i0 + li, gj = j0 + lj;
-            float vw = 0.0f, vrx = 0.0f, vry = 0.0f, vpx = 0.0f, vpy = 0.0f;
-            if (gi >= 0 && gi < ny && gj >= 0 && gj < nx) {
+        const int gj = j0 + lj;
+        const bool jin = gj >= 0 && gj < nx;
+        const bool fx = gj >= 0 && gj < nx - 1;  // x-gradient kept (forward difference inside the image)
+        float w[kTvM], rx[kTvM], ry[kTvM], px[kTvM], py[kTvM], xv[kTvM];
+        unsigned fy = 0u;  // bit m: y-gradient kept at row tr + kTvRows m
+#pragma unroll
+        for (int m = 0; m < kTvM; ++m) {
+            const int li = tr + kTvRows * m, gi = i0 + li;
+            if (gi >= 0 && gi < ny - 1) fy |= 1u << m;
+            w[m] = rx[m] = ry[m] = px[m] = py[m] = 0.0f;
+            if (jin && gi >= 0 && gi < ny) {
                 const long long q = (long long)gi * nx + gj;
-                vw = __ldcg(a.w + q);
-                vrx = __ldcg(rx + q);
-                vry = __ldcg(ry + q);
-                vpx = __ldcg(px + q);
-                vpy = __ldcg(py + q);
+                w[m] = __ldcg(a.w + q);
+                rx[m] = __ldcg(rxg + q);
+                ry[m] = __ldcg(ryg + q);
+                px[m] = __ldcg(pxg + q);
+                py[m] = __ldcg(pyg + q);
             }
-            sm.w[li][lj] = vw;
-            sm.rx[li][lj] = vrx;
-            sm.ry[li][lj] = vry;
-            sm.px[li][lj] = vpx;
-            sm.py[li][lj] = vpy;
+            sm.rx[tv_ri(li, lj)] = rx[m];
+            sm.ry[tv_ri(li, lj)] = ry[m];
         }
         __syncthreads();
         for (int k = 0; k < nsteps; ++k) {
             const float beta = s_beta[k];
-            // x = w + theta div r (region positions without a neighbour take 0:
-            // they are in the garbage ring or outside the image, unused)
-            for (int e = threadIdx.x; e < kTvR * kTvR; e += kTvThreads) {
-                const int li = e / kTvR, lj = e % kTvR, gi = i0 + li, gj = j0 + lj;
-                float dv = 0.0f;
-                if (gj < nx - 1) dv += sm.rx[li][lj];
-                if (gj > 0 && lj > 0) dv -= sm.rx[li][lj - 1];
-                if (gi < ny - 1) dv += sm.ry[li][lj];
-                if (gi > 0 && li > 0) dv -= sm.ry[li - 1][lj];
-                sm.x[li][lj] = fmaf(theta, dv, sm.w[li][lj]);
+            // x = w + theta div r
+#pragma unroll
+            for (int m = 0; m < kTvM; ++m) {
+                const int li = tr + kTvRows * m;
+                const float dv = ((rx[m] - sm.rx[tv_ri(li, lj - 1)]) + ry[m]) - sm.ry[tv_ri(li - 1, lj)];
+                xv[m] = fmaf(theta, dv, w[m]);
+                sm.x[li * kTvR + lj] = xv[m];
             }
             __syncthreads();
-            // (p, r) update from grad x, in place (each position reads only its own p, r)
-            for (int e = threadIdx.x; e < kTvR * kTvR; e += kTvThreads) {
-                const int li = e / kTvR, lj = e % kTvR, gi = i0 + li, gj = j0 + lj;
-                const float x0 = sm.x[li][lj];
-                const float gx = (gj < nx - 1 && lj + 1 < kTvR) ? sm.x[li][lj + 1] - x0 : 0.0f;
-                const float gy = (gi < ny - 1 && li + 1 < kTvR) ? sm.x[li + 1][lj] - x0 : 0.0f;
-                const float qx = fmaf(step, gx, sm.rx[li][lj]);
-                const float qy = fmaf(step, gy, sm.ry[li][lj]);
-                const float nrm = fmaxf(1.0f, sqrtf(qx * qx + qy * qy));
-                const float nx_ = qx / nrm, ny_ = qy / nrm;
-                sm.rx[li][lj] = fmaf(beta, nx_ - sm.px[li][lj], nx_);
-                sm.ry[li][lj] = fmaf(beta, ny_ - sm.py[li][lj], ny_);
-                sm.px[li][lj] = nx_;
-                sm.py[li][lj] = ny_;
+            // (p, r) update from grad x
+#pragma unroll
+            for (int m = 0; m < kTvM; ++m) {
+                const int li = tr + kTvRows * m;
+                const float x0 = xv[m];
+                // neighbours loaded unconditionally (always inside the arrays), then masked
+                const float xe = sm.x[li * kTvR + lj + 1], xs = sm.x[(li + 1) * kTvR + lj];
+                const float gx = fx ? xe - x0 : 0.0f;
+                const float gy = (fy >> m) & 1u ? xs - x0 : 0.0f;
+                const float qx = fmaf(step, gx, rx[m]);
+                const float qy = fmaf(step, gy, ry[m]);
+                // projection onto the unit disc: q / max(1, |q|), with the
+                // hardware reciprocal square root where |q| > 1
+                const float s2 = fmaf(qx, qx, qy * qy);
+                const float inv = s2 > 1.0f ? rsqrtf(s2) : 1.0f;
+                const float nx_ = qx * inv, ny_ = qy * inv;
+                rx[m] = fmaf(beta, nx_ - px[m], nx_);
+                ry[m] = fmaf(beta, ny_ - py[m], ny_);
+                px[m] = nx_;
+                py[m] = ny_;
+                // read by the neighbours in the next x update, after the barrier
+                sm.rx[tv_ri(li, lj)] = rx[m];
+                sm.ry[tv_ri(li, lj)] = ry[m];
             }
             __syncthreads();
         }
         // the tile (exact after nsteps <= kTvK steps) to the second buffers
-        for (int e = threadIdx.x; e < kTvT * kTvT; e += kTvThreads) {
-            const int li = kTvK + e / kTvT, lj = kTvK + e % kTvT, gi = i0 + li, gj = j0 + lj;
-            if (gi < ny && gj < nx) {
-                const long long q = (long long)gi * nx + gj;
-                px2[q] = sm.px[li][lj];
-                py2[q] = sm.py[li][lj];
-                rx2[q] = sm.rx[li][lj];
-                ry2[q] = sm.ry[li][lj];
+        if (jin && lj >= kTvK && lj < kTvK + kTvT) {
+#pragma unroll
+            for (int m = 0; m < kTvM; ++m) {
+                const int li = tr + kTvRows * m, gi = i0 + li;
+                if (li >= kTvK && li < kTvK + kTvT && gi < ny) {
+                    const long long q = (long long)gi * nx + gj;
+                    px2[q] = px[m];
+                    py2[q] = py[m];
+                    rx2[q] = rx[m];
+                    ry2[q] = ry[m];
+                }
             }
         }
-        __syncthreads();
     }
     t = s_t;
     __syncthreads();  // s_t and s_beta are rewritten by the next call
@@ -265,6 +314,10 @@ __global__ void __launch_bounds__(kTvThreads, 2) k_tv_project(TvArgs a)
     if (a.done && ld_volatile_i32(a.done)) return;
     extern __shared__ __align__(16) unsigned char tv_smem[];
     TvSmem &sm = *reinterpret_cast<TvSmem *>(tv_smem);
+    // the pads of the dual-step arrays are never written after this
+    for (int e = threadIdx.x; e < (int)(sizeof(TvSmem) / sizeof(float)); e += kTvThreads)
+        reinterpret_cast<float *>(tv_smem)[e] = 0.0f;
+    __syncthreads();
     const long long stride = (long long)gridDim.x * kTvThreads;
     const long long first = (long long)blockIdx.x * kTvThreads + threadIdx.x;
     const int nx = a.nx, ny = a.ny;
@@ -289,7 +342,7 @@ __global__ void __launch_bounds__(kTvThreads, 2) k_tv_project(TvArgs a)
         double tw = 0.0;
         if (!a.fixed_lam) {
             for (long long q = first; q < a.d; q += stride)
-                part += tv_term(a.w, (int)(q / nx), (int)(q % nx), nx, ny);
+                part += tv_term(a.w, tv_row(q, nx), tv_col(q, nx), nx, ny);
             tw = grid_sum(a, part, slot, ok);
             slot ^= 1;
             if (!ok) return;
@@ -317,7 +370,7 @@ __global__ void __launch_bounds__(kTvThreads, 2) k_tv_project(TvArgs a)
                     tp = ry; ry = ry2; ry2 = tp;
                 }
                 for (long long q = first; q < a.d; q += stride)
-                    a.xt[q] = prox_x(a.w, px, py, theta, (int)(q / nx), (int)(q % nx), nx, ny);
+                    a.xt[q] = prox_x(a.w, px, py, theta, tv_row(q, nx), tv_col(q, nx), nx, ny);
                 if (!grid_barrier(a.bar, a.err, a.done)) return;
                 if (a.fixed_lam) {
                     ++solves;
@@ -325,7 +378,7 @@ __global__ void __launch_bounds__(kTvThreads, 2) k_tv_project(TvArgs a)
                 }
                 part = 0.0;
                 for (long long q = first; q < a.d; q += stride)
-                    part += tv_term(a.xt, (int)(q / nx), (int)(q % nx), nx, ny);
+                    part += tv_term(a.xt, tv_row(q, nx), tv_col(q, nx), nx, ny);
                 const double tx = grid_sum(a, part, slot, ok);
                 slot ^= 1;
                 if (!ok) return;
@@ -358,7 +411,7 @@ __global__ void __launch_bounds__(kTvThreads, 2) k_tv_project(TvArgs a)
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (long long q = first; q < a.d; q += stride) {
         const float v = __ldcg(a.zk + q);
-        const int i = (int)(q / nx), j = (int)(q - (long long)i * nx);
+        const int i = tv_row(q, nx), j = tv_col(q, nx);
         if (a.old_r) {  // read before out_r, which may be the same image
             const double xb = (double)__ldcg(a.old_r + (long long)i * a.ldr + j + kPad);
             const double dd = (double)v - xb;
