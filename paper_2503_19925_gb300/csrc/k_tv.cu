@@ -353,15 +353,12 @@ __global__ void __launch_bounds__(kTvThreads, 2) k_tv_project(TvArgs a)
             for (int s = 0; s < a.max_bisect; ++s) {
                 const float theta = (float)(0.5 * lam);
                 const float step = (float)(1.0 / (4.0 * lam));  // 1 / (8 theta)
-                for (long long q = first; q < a.d; q += stride) {
-                    rx[q] = __ldcg(px + q);
-                    ry[q] = __ldcg(py + q);
-                }
-                if (!grid_barrier(a.bar, a.err, a.done)) return;
                 double t = 1.0;
                 for (int it = 0; it < a.fgp_iters; it += kTvK) {
                     const int ns = a.fgp_iters - it < kTvK ? a.fgp_iters - it : kTvK;
-                    fgp_block(a, sm, rx, ry, px, py, px2, py2, rx2, ry2, theta, step, t, ns);
+                    // the first block starts r at p, the carried dual
+                    fgp_block(a, sm, it == 0 ? px : rx, it == 0 ? py : ry, px, py, px2, py2, rx2, ry2, theta, step,
+                              t, ns);
                     if (!grid_barrier(a.bar, a.err, a.done)) return;
                     float *tp;
                     tp = px; px = px2; px2 = tp;
@@ -369,16 +366,25 @@ __global__ void __launch_bounds__(kTvThreads, 2) k_tv_project(TvArgs a)
                     tp = rx; rx = rx2; rx2 = tp;
                     tp = ry; ry = ry2; ry2 = tp;
                 }
-                for (long long q = first; q < a.d; q += stride)
-                    a.xt[q] = prox_x(a.w, px, py, theta, tv_row(q, nx), tv_col(q, nx), nx, ny);
-                if (!grid_barrier(a.bar, a.err, a.done)) return;
+                // x = w + theta div p, and its TV from the neighbours' x
+                // recomputed in place (the same FP32 values), so no barrier
+                // separates the two; later phases read xt only at the pixel
+                // each thread wrote
+                part = 0.0;
+                for (long long q = first; q < a.d; q += stride) {
+                    const int i = tv_row(q, nx), j = tv_col(q, nx);
+                    const float c = prox_x(a.w, px, py, theta, i, j, nx, ny);
+                    a.xt[q] = c;
+                    if (!a.fixed_lam) {
+                        const float gx = j < nx - 1 ? prox_x(a.w, px, py, theta, i, j + 1, nx, ny) - c : 0.0f;
+                        const float gy = i < ny - 1 ? prox_x(a.w, px, py, theta, i + 1, j, nx, ny) - c : 0.0f;
+                        part += sqrt((double)gx * gx + (double)gy * gy);
+                    }
+                }
                 if (a.fixed_lam) {
                     ++solves;
                     break;
                 }
-                part = 0.0;
-                for (long long q = first; q < a.d; q += stride)
-                    part += tv_term(a.xt, tv_row(q, nx), tv_col(q, nx), nx, ny);
                 const double tx = grid_sum(a, part, slot, ok);
                 slot ^= 1;
                 if (!ok) return;
