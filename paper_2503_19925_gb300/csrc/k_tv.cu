@@ -187,13 +187,15 @@ __device__ __forceinline__ float prox_x(const float *w, const float *rx, const f
 // (m < kTvM); its w, r, p and x stay in registers, and only r and x, which
 // the neighbours read, go through shared memory.  The boundary rule needs no
 // branch in the divergence: r_x is zero at the last image column and r_y at
-// the last row (their gradient components are zero there, and the duals start
-// at zero), and every position outside the image is staged as zero with its
-// gradient components masked, so the terms the rule drops are exact zeros.
+// the last row (their gradient components are zero there, so they keep the
+// zero every dual starts with, and p carried between solves keeps it too),
+// and every position outside the image is staged as zero with its gradient
+// components masked, so the terms the rule drops are exact zeros.
 // The shared arrays are flat with row stride kTvR (= 16 mod 32 words, no bank
 // conflicts across the two rows a warp touches); r has one leading pad row and
-// column, x one trailing: region-edge reads land on the pad or on another
-// edge position, and feed only the garbage ring.
+// column, x one trailing (zeroed once per launch, never written): region-edge
+// reads land on the pad or on another edge position, and feed only the
+// garbage ring.
 constexpr int kTvT = 32, kTvK = 8, kTvR = kTvT + 2 * kTvK;
 constexpr int kTvRows = kTvThreads / kTvR;  // rows of the region per pass of the CTA
 constexpr int kTvM = kTvR / kTvRows;        // region positions per thread
