@@ -60,6 +60,11 @@ def parse_args(argv=None):
     p.add_argument("--no-gaussian", action="store_true", help="skip the Gaussian-model (Fig. 6) measurement")
     p.add_argument("--serve-jobs", type=int, default=32)
     p.add_argument("--serve-round-iters", type=int, default=20, help="iterations per server round")
+    p.add_argument("--serve-scale", choices=sorted(SERVE_SCALES), default="small",
+                   help="served stream ranges: small (the default run) or full (image sizes to 1024^2, 1440 views, "
+                        "tolerance 1e-4)")
+    p.add_argument("--serve-sat-work", type=float, default=4e8,
+                   help="server admission limit: resident nonzeros of A per iteration (inf: every job that fits)")
     p.add_argument("--serve-loads", default="0.8,1.5",
                    help="arrival rates as fractions of the measured sequential capacity")
     return p.parse_args(argv)
@@ -262,21 +267,31 @@ def make_counts(ex, torch, spec, dev, rank=0):
     return plan, y, mu, S, xs
 
 
-def run_served(ex, torch, dev, n_jobs: int, loads, rank: int, round_iters: int = 20):
+# served stream scales: image sizes, views, tolerance, iteration cap
+SERVE_SCALES = {
+    "small": dict(sizes=(128, 512), views=(90, 720), tol=1e-3, max_iters=1000),   # the default run: minutes
+    "full": dict(sizes=(128, 1024), views=(90, 1440), tol=1e-4, max_iters=3000),  # the C5 ranges
+}
+
+
+def run_served(ex, torch, dev, n_jobs: int, loads, rank: int, round_iters: int = 20, scale: str = "small",
+               sat_work: float = 4e8):
     """A Poisson stream of reconstruction requests (image sizes 128..512,
     90..720 views, parallel or fan beam, 1..4 windows, 16..64 energies,
-    tolerance 1e-3) served (a) by the continuous-batching Server and (b) one at
-    a time with exact_solve, at an arrival rate of `load` times the measured
-    one-at-a-time capacity.  Plan building, upload and the step-size estimate
-    of each request are inside the served time in both cases."""
+    tolerance 1e-3; scale "full": 128..1024, 90..1440 views, tolerance 1e-4)
+    served (a) by the continuous-batching Server and (b) one at a time with
+    exact_solve, at an arrival rate of `load` times the measured one-at-a-time
+    capacity.  Plan building, upload and the step-size estimate of each request
+    are inside the served time in both cases."""
     from paper_2503_19925_gb300.serve import Request, Server, serve_sequential
-    specs = configs.c5_requests(n_jobs, sizes=(128, 512), views=(90, 720))
+    sc = SERVE_SCALES[scale]
+    specs = configs.c5_requests(n_jobs, sizes=sc["sizes"], views=sc["views"])
     reqs, truth = [], {}
     for k, sp in enumerate(specs):
         plan, y, mu, S, xs = make_counts(ex, torch, sp, dev, rank)
         plan.close()
         reqs.append(Request(ex.Geometry(**sp["geometry"]), list(mu), S.tolist(), y.cpu().pin_memory(), sp["I0"],
-                            tol=1e-3, max_iters=1000, tag=k))
+                            tol=sc["tol"], max_iters=sc["max_iters"], tag=k))
         truth[k] = xs
     torch.cuda.synchronize()
 
@@ -301,7 +316,8 @@ def run_served(ex, torch, dev, n_jobs: int, loads, rank: int, round_iters: int =
         for r in reqs:
             t += float(rng.exponential(1.0 / rate))
             r.arrival = t
-        server = Server(budget_bytes=configs.C5["budget_bytes"], max_slots=64, round_iters=round_iters)
+        server = Server(budget_bytes=configs.C5["budget_bytes"], max_slots=64, round_iters=round_iters,
+                        sat_work=sat_work)
         served = summarise(server.run(reqs, realtime=True))
         served["rounds"] = server.rounds
         server.close()
@@ -310,8 +326,10 @@ def run_served(ex, torch, dev, n_jobs: int, loads, rank: int, round_iters: int =
                        "sequential": plain, "speedup_recon_per_s": served["recon_per_s"] / plain["recon_per_s"],
                        "p99_latency_ratio": plain["p99_latency_s"] / served["p99_latency_s"]})
     return {"requests": n_jobs, "sequential_capacity_per_s": cap,
-            "workload": "Poisson stream; 128..512^2, 90..720 views, parallel/fan 50/50, 1..4 windows, 16..64 "
-                        f"energies, tol 1e-3, HBM budget 150 GB, {round_iters} iterations per round",
+            "workload": f"Poisson stream; {sc['sizes'][0]}..{sc['sizes'][1]}^2, {sc['views'][0]}..{sc['views'][1]} "
+                        "views, parallel/fan 50/50, 1..4 windows, 16..64 "
+                        f"energies, tol {sc['tol']:g}, HBM budget 150 GB, {round_iters} iterations per round, "
+                        f"admission up to {sat_work:g} nonzeros of A per iteration",
             "loads": points}
 
 
@@ -690,7 +708,7 @@ def run_exact(args):
     if not args.no_served:
         line["served"] = run_served(ex, torch, dev, args.serve_jobs,
                                     [float(v) for v in args.serve_loads.split(",") if v], rank,
-                                    args.serve_round_iters)
+                                    args.serve_round_iters, args.serve_scale, args.serve_sat_work)
     if not args.no_tv:
         line["tv"] = run_tv(ex, torch, dev, rank)
     if not args.no_gaussian:

@@ -2,8 +2,12 @@
 
 A request carries a scan geometry, the energy attenuations and window weights,
 the counts (on the host), the source intensity, a relative-residual tolerance
-and an iteration cap.  The loop admits waiting requests while their device
-footprint fits the HBM budget and a batch slot is free: it builds the plan,
+and an iteration cap.  The loop admits waiting requests, first come first
+served, while their device footprint fits the HBM budget, a batch slot is free
+and the resident jobs' work per iteration (nonzeros of A) stays below what
+fills the GPU on its own (`sat_work`, about one 512^2 x 720-view fan scan:
+past that, interleaving more jobs adds latency but no throughput, so larger
+jobs run one after another): it builds the plan,
 binds a workspace, uploads the counts, estimates ||A||^2 (FP32 power
 iteration) for the step size 1/(4L), and keeps all of it resident.  Every
 round runs `round_iters` extragradient iterations of all resident jobs in one
@@ -11,8 +15,10 @@ persistent launch (exact_batch_solve); a job resumes from its own iterate, so a
 round boundary changes nothing in its arithmetic.  After a round the loop reads
 each job's residual, retires the converged ones (their memory is freed) and
 admits new arrivals, which therefore overlap on the device with the jobs
-already running.  (The batch runs one CTA per adjoint tile, so the per-plan
-autotuner is not needed here; the one-at-a-time baseline below uses it.)
+already running.  A round with a single resident job runs it with
+exact_solve instead, with the adjoint split autotuned for its shape (the
+persistent kernel runs one CTA per adjoint tile, which only pays when several
+jobs share the GPU).
 
 This is host orchestration only: all arithmetic runs in libexact.so.
 """
@@ -72,6 +78,14 @@ class _Active:
     footprint: int
     iters: int = 0
     admitted: float = 0.0
+    work: float = 0.0
+    tuned: bool = False
+
+
+def work_per_iter(geometry: Geometry) -> float:
+    """Nonzeros of A, about rays x the driving-axis length (an estimate of
+    the gather work of one forward or adjoint)."""
+    return float(geometry.n_views) * geometry.n_bins * max(geometry.nx, geometry.ny)
 
 
 def footprint_bytes(geometry: Geometry, W: int, y_itemsize: int) -> int:
@@ -93,8 +107,10 @@ class Server:
     """Continuous-batching EXACT server on the current CUDA device."""
 
     def __init__(self, budget_bytes: float = 150e9, max_slots: int = 64, round_iters: int = 20,
-                 norm_iters: int = 60, norm_rtol: float = 1e-5):
+                 norm_iters: int = 60, norm_rtol: float = 1e-5, sat_work: float = 4e8):
         self.budget = int(budget_bytes)
+        self.sat_work = float(sat_work)
+        self.work = 0.0
         self.max_slots = max_slots
         self.round_iters = round_iters
         self.norm_iters = norm_iters
@@ -119,14 +135,18 @@ class Server:
             need = footprint_bytes(req.geometry, len(req.S), req.y.element_size())
             if self.used + need > self.budget and self.active:
                 break  # wait for memory to free up
+            w = work_per_iter(req.geometry)
+            if self.active and self.work + w > self.sat_work:
+                break  # the GPU is full: wait for a job to finish
             self.waiting.popleft()
             plan = Plan(req.geometry, req.mu, req.S)
             y = req.y.to(plan.device, non_blocking=True).contiguous()
             x = torch.zeros(plan.shape_img, dtype=torch.float32, device=plan.device)
             lam, _ = plan.norm_estimate_f32(self.norm_iters, self.norm_rtol)
             eta = plan.recommended_eta(req.I0, lam)
-            self.active.append(_Active(req, plan, y, x, eta, need, 0, self.now()))
+            self.active.append(_Active(req, plan, y, x, eta, need, 0, self.now(), w))
             self.used += need
+            self.work += w
             self.peak_used = max(self.peak_used, self.used)
 
     def step(self) -> list[Result]:
@@ -139,7 +159,16 @@ class Server:
             k = min(self.round_iters, a.req.max_iters - a.iters)
             jobs.append(Job(plan=a.plan, y=a.y, I0=a.req.I0, eta=a.eta, iters=k, x=a.x, lo=a.req.lo, hi=a.req.hi,
                             tol=a.req.tol, check_every=a.req.check_every))
-        _, infos = self.batch.solve(jobs, sync=True)
+        if len(self.active) == 1:
+            a, jb = self.active[0], jobs[0]
+            if not a.tuned:
+                a.plan.autotune()
+                a.tuned = True
+            _, info = a.plan.solve(jb.y, jb.I0, jb.eta, jb.iters, x=jb.x, lo=jb.lo, hi=jb.hi, tol=jb.tol,
+                                   check_every=jb.check_every, sync=True)
+            infos = [info]
+        else:
+            _, infos = self.batch.solve(jobs, sync=True)
         self.rounds += 1
         done, keep = [], []
         for a, jb, info in zip(self.active, jobs, infos):
@@ -152,6 +181,7 @@ class Server:
                 done.append(res)
                 a.plan.close()
                 self.used -= a.footprint
+                self.work -= a.work
             else:
                 keep.append(a)
         self.active = keep

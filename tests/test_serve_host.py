@@ -17,6 +17,23 @@ class FakeInfo:
         self.iters_done, self.rel_res, self.status = iters, rel, status
 
 
+def _advance(plan, iters, tol):
+    """A job's residual halves every iteration from 1.0; a plan marked bad
+    reports a non-finite residual."""
+    done = getattr(plan, "progress", 0)
+    if getattr(plan, "bad", False):
+        return FakeInfo(1, float("nan"), 5)
+    k = 0
+    rel = 0.5 ** done
+    while k < iters:
+        k += 1
+        rel = 0.5 ** (done + k)
+        if tol > 0 and rel <= tol:
+            break
+    plan.progress = done + k
+    return FakeInfo(k, rel)
+
+
 class FakePlan:
     live = 0
 
@@ -33,6 +50,14 @@ class FakePlan:
 
     def norm_estimate_f32(self, iters, rtol):
         return 100.0, 5
+
+    solo_calls = 0
+
+    def solve(self, y, I0, eta, iters, x=None, lo=0.0, hi=math.inf, tol=0.0, check_every=1, sync=True):
+        import time
+        FakePlan.solo_calls += 1
+        time.sleep(0.002)
+        return x, _advance(self, iters, tol)
 
     def recommended_eta(self, I0, lam):
         return 0.1
@@ -54,21 +79,7 @@ class FakeBatch:
         import time
         self.calls.append(len(jobs))
         time.sleep(0.002)
-        infos = []
-        for jb in jobs:
-            done = getattr(jb.plan, "progress", 0)
-            if getattr(jb.plan, "bad", False):
-                infos.append(FakeInfo(1, float("nan"), 5))
-                continue
-            k = 0
-            rel = 0.5 ** done
-            while k < jb.iters:
-                k += 1
-                rel = 0.5 ** (done + k)
-                if jb.tol > 0 and rel <= jb.tol:
-                    break
-            jb.plan.progress = done + k
-            infos.append(FakeInfo(k, rel))
+        infos = [_advance(jb.plan, jb.iters, jb.tol) for jb in jobs]
         return [jb.x for jb in jobs], infos
 
     def close(self):
@@ -80,6 +91,7 @@ def fakes(monkeypatch):
     monkeypatch.setattr(serve, "Plan", FakePlan)
     monkeypatch.setattr(serve, "Batch", FakeBatch)
     FakePlan.live = 0
+    FakePlan.solo_calls = 0
     yield
 
 
@@ -105,7 +117,8 @@ def test_budget_admits_one_at_a_time():
     one = serve.footprint_bytes(reqs[0].geometry, 1, 4)
     s = serve.Server(budget_bytes=one * 1.5, max_slots=8, round_iters=4)
     res = s.run(reqs, realtime=False)
-    assert len(res) == 3 and max(s.batch.calls) == 1
+    assert len(res) == 3 and s.batch.calls == []  # one job resident at a time: plain solves
+    assert FakePlan.solo_calls == s.rounds
     assert s.peak_used <= one * 1.5
 
 
@@ -132,3 +145,30 @@ def test_late_arrivals_join_running_batch():
     res = {r.tag: r for r in s.run(reqs, realtime=True)}
     assert set(res) == {"early", "late0", "late1"}
     assert max(s.batch.calls) == 3  # the late requests ran alongside the early one
+
+
+def test_saturating_jobs_run_one_after_another():
+    """Jobs whose work alone reaches the admission limit are not interleaved:
+    each runs its rounds alone, through the plain solve, in arrival order."""
+    reqs = [_req(16, tol=1e-3, tag=k) for k in range(3)]
+    work = serve.work_per_iter(reqs[0].geometry)
+    srv = serve.Server(budget_bytes=1e12, max_slots=8, round_iters=4, sat_work=work)
+    res = srv.run(reqs, realtime=False)
+    srv.close()
+    assert sorted(r.tag for r in res) == [0, 1, 2]
+    assert srv.batch.calls == []  # never more than one job resident
+    assert FakePlan.solo_calls == srv.rounds
+    assert [r.tag for r in sorted(res, key=lambda r: r.finished)] == [0, 1, 2]
+    assert all(r.admitted >= prev.finished for prev, r in zip(sorted(res, key=lambda r: r.finished),
+                                                               sorted(res, key=lambda r: r.finished)[1:]))
+
+
+def test_small_jobs_share_rounds_below_the_limit():
+    reqs = [_req(16, tol=1e-3, tag=k) for k in range(3)]
+    work = serve.work_per_iter(reqs[0].geometry)
+    srv = serve.Server(budget_bytes=1e12, max_slots=8, round_iters=4, sat_work=3 * work)
+    res = srv.run(reqs, realtime=False)
+    srv.close()
+    assert sorted(r.tag for r in res) == [0, 1, 2]
+    assert max(srv.batch.calls) == 3  # all three in one persistent launch
+
