@@ -58,6 +58,8 @@ def parse_args(argv=None):
     p.add_argument("--no-served", action="store_true", help="skip the serving measurement")
     p.add_argument("--no-tv", action="store_true", help="skip the TV-ball feasible-set measurement")
     p.add_argument("--no-gaussian", action="store_true", help="skip the Gaussian-model (Fig. 6) measurement")
+    p.add_argument("--no-extensions", action="store_true",
+                   help="skip the known-background / running-average / proximal-variant timings")
     p.add_argument("--serve-jobs", type=int, default=32)
     p.add_argument("--serve-round-iters", type=int, default=20, help="iterations per server round")
     p.add_argument("--serve-scale", choices=sorted(SERVE_SCALES), default="small",
@@ -440,6 +442,60 @@ def run_tv(ex, torch, dev, rank: int):
     return out
 
 
+def run_extensions(ex, torch, dev, rank: int, iters: int = 50):
+    """The solve options beyond the box-constrained path, each timed on the
+    512^2 fan workload (CUDA events, `iters` iterations after one warm-up
+    call, no tolerance stop): a known background material (Appendix A.1:
+    one material whose projections enter every ray's attenuation), the
+    paper's running-average output and stopping rule (Sec. 3.1), and the
+    proximal variant with l_X = TV (Sec. 5)."""
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()  # warm
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    cfg, S, mu, xs, seed = workload("C3")
+    plan = ex.Plan(ex.Geometry(**cfg["geometry"]), mu, S)
+    plan.autotune()
+    zt = plan.forward(torch.tensor(xs, dtype=torch.float32, device=dev)).double()
+    lam = cfg["I0"] * torch.einsum("wk,kvb->wvb", torch.tensor(S, dtype=torch.float64, device=dev),
+                                   torch.exp(-torch.tensor(mu, dtype=torch.float64, device=dev)[:, None, None]
+                                             * zt.clamp_min(0)[None]))
+    gen = torch.Generator(device=dev).manual_seed(seed + 1 + 7919 * rank)
+    y = torch.poisson(lam, generator=gen).to(torch.bfloat16).contiguous()
+    normA, _ = plan.norm_estimate(max_iters=100, rtol=1e-6)
+    eta = plan.recommended_eta(cfg["I0"], normA)
+    x = torch.zeros_like(torch.tensor(xs, dtype=torch.float32, device=dev))
+
+    def run(**kw):
+        x.zero_()
+        plan.solve(y, cfg["I0"], eta, iters, x=x, sync=False, **kw)
+
+    base = timed(run)
+    out["box"] = {"iters": iters, "ms_per_iter": base / iters}
+    # known background: a second phantom of another material, projected by the plan
+    bg = synth.rasterize_ellipses(synth.random_ellipses(xs.shape[0], 3, seed + 11), xs.shape[1], xs.shape[0],
+                                  supersample=2)
+    pb = plan.forward(torch.tensor(0.3 * bg, dtype=torch.float32, device=dev))[None].contiguous()
+    plan.set_background([[0.5 * m for m in mu]], pb)
+    out["known_background"] = {"iters": iters, "ms_per_iter": timed(run) / iters, "materials": 1}
+    plan.set_background()
+    out["running_average"] = {"iters": iters, "ms_per_iter": timed(lambda: run(stop_rule="average")) / iters}
+    out["proximal_tv"] = {"iters": iters, "ms_per_iter": timed(lambda: run(prox_lambda=0.05)) / iters,
+                          "lambda": 0.05, "fgp_iters": 40}
+    plan.close()
+    out["workload"] = describe(cfg)
+    return out
+
+
 def run_gaussian(ex, torch, dev):
     """The experiment of Sec. 3.2 / Fig. 6 on the GPU (dense FP64 path):
     Gaussian a_i, noiseless monochromatic counts (I0 = 1, mu = 1), d = 100,
@@ -713,6 +769,8 @@ def run_exact(args):
         line["tv"] = run_tv(ex, torch, dev, rank)
     if not args.no_gaussian:
         line["gaussian"] = run_gaussian(ex, torch, dev)
+    if not args.no_extensions:
+        line["extensions"] = run_extensions(ex, torch, dev, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_baseline_iters)
     if rank == 0:
