@@ -3,7 +3,6 @@ and the oracle: a job's result is bitwise the same alone and in any mix, and
 matches the single-job path and the FP64 oracle within the solve tolerances."""
 import math
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

@@ -8,7 +8,6 @@ that rounding); the returned average is compared like a whole solve
 (relative L2 <= 1e-3, PSNR within 0.05 dB)."""
 import math
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

@@ -6,7 +6,6 @@ arrivals join while earlier requests run.  Also the FP32 power iteration
 against the FP64 one."""
 import math
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

@@ -7,7 +7,6 @@ autotuner must pick a listed value and reuse it for a plan of the same shape.
 """
 import math
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

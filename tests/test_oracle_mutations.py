@@ -6,7 +6,6 @@ against it in a subprocess; the run must fail.  The unmodified source must
 pass the same selection (checked by the rest of the suite).
 """
 import os
-import shutil
 import subprocess
 import sys
 

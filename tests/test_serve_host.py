@@ -2,8 +2,6 @@
 admission by memory budget and slots, round scheduling, retirement on the
 tolerance, iteration caps, failing jobs, arrivals that join mid-run."""
 import math
-import sys
-import types
 
 import pytest
 
