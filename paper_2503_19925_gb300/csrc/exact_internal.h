@@ -79,7 +79,7 @@ struct __align__(16) ViewRec {
 constexpr int kFR = 128;   // rays per unit (threads per CTA)
 constexpr int kFC = 16;    // driving lines per staged chunk
 constexpr int kFStages = 2;  // staging buffers (copies kFStages - 1 chunks ahead)
-constexpr int kFHB = 256;  // staged cross-axis rows per chunk (tensor-map box height)
+constexpr int kFHB = 192;  // staged cross-axis rows per chunk (tensor-map box height)
 // Adjoint tile (pixels): one CTA gathers A^T r over kTW x kTH pixels.
 constexpr int kTW = 16;
 constexpr int kTH = 16;
