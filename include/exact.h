@@ -10,7 +10,8 @@
  * notation list) and m = W * n the number of (window, ray) measurements.
  *
  * Conventions shared by every call:
- *  - Images are FP32 (FP64 only inside exact_norm_estimate), row-major
+ *  - Images are FP32 (FP64 inside exact_norm_estimate and on the dense
+ *    exact_dense_* path), row-major
  *    [ny][nx]; pixel (ix, iy) has its centre at ((ix-(nx-1)/2) p, (iy-(ny-1)/2) p)
  *    with p = geometry.pixel.
  *  - Sinograms are [n_views][n_bins] (bins fastest); counts are
@@ -30,7 +31,9 @@
  *    small pinned host buffer; per-call scratch lives in a caller-allocated
  *    workspace bound with exact_plan_bind_workspace.
  *  - Calls taking a stream enqueue work on it and return without waiting,
- *    except exact_plan_create and exact_norm_estimate, which synchronise.
+ *    except those that hand a device result to the host (the norm
+ *    estimates, the autotuners), which synchronise; so do the create and
+ *    destroy calls.
  *    Every call validates its arguments and returns a status; none aborts,
  *    traps or prints.  A plan is used from one host thread at a time and on
  *    the device that was current when it was created.
