@@ -37,8 +37,14 @@ from synth import configs  # noqa: E402
 METRIC = "EXACT iters/s at 512^2x720 views"
 UNIT = "iter/s"
 L2_FLUSH_BYTES = 256 << 20
-SMS = 152
-L1_WORDS_PER_CLK = 32  # 128 B/clk/SM L1/shared data path = 32 FP32 words
+L1_WORDS_PER_CLK = 32  # 128 B/clk/SM L1/shared data path = 32 FP32 words (nominal figure)
+L2_NOTE = "flushed before every timed step (256 MiB write outside the timed events)"
+
+
+def bench_config(cfg, world: int) -> dict:
+    """The `config` of the JSON line, the same for both arms."""
+    return {"workload": describe(cfg), "iters_per_solve": cfg["iters"], "l2": L2_NOTE,
+            "parallelism": f"{world} independent replicas" if world > 1 else "single device"}
 
 
 def parse_args(argv=None):
@@ -69,6 +75,8 @@ def parse_args(argv=None):
                    help="server admission limit: resident nonzeros of A per iteration (inf: every job that fits)")
     p.add_argument("--serve-loads", default="0.8,1.5",
                    help="arrival rates as fractions of the measured sequential capacity")
+    p.add_argument("--serve-mode", choices=["streams", "rounds"], default="streams",
+                   help="server mode: each job's solve on its own stream, or persistent-kernel rounds")
     return p.parse_args(argv)
 
 
@@ -176,7 +184,12 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- reference (oracle) arm
 
-def oracle_inputs(cfg_name: str):
+def oracle_inputs(cfg_name: str, norm_iters: int = 3):
+    """The workload's counts drawn from the oracle's own projector and link
+    (Poisson, seeded; BF16-rounded where the workload stores BF16), and the
+    step 1/(4L) from `norm_iters` oracle power iterations (None for 0).  The
+    CPU legs of the benchmark and the stored oracle solves of tests/golden use
+    these inputs."""
     import oracle
     cfg, S, mu, xs, seed = workload(cfg_name)
     g = oracle.Geometry(**cfg["geometry"])
@@ -185,13 +198,17 @@ def oracle_inputs(cfg_name: str):
     if cfg["y_dtype"] == "bf16":
         import torch
         y = torch.from_numpy(y).to(torch.bfloat16).to(torch.float64).numpy()
-    nA, _ = oracle.norm_estimate(g, 3, 0.0)  # the step size does not change the work timed
-    eta = 1.0 / (4.0 * oracle.lipschitz(nA, S, mu, cfg["I0"], cfg["W"] * g.n_rays))
+    eta = None
+    if norm_iters > 0:
+        nA, _ = oracle.norm_estimate(g, norm_iters, 0.0)
+        eta = 1.0 / (4.0 * oracle.lipschitz(nA, S, mu, cfg["I0"], cfg["W"] * g.n_rays))
     return oracle, cfg, g, S, mu, y, eta
 
 
 def cpu_baseline(cfg_name: str, iters: int):
-    """The oracle as it stands, timed on this host's cores for a few iterations."""
+    """The oracle as it stands, timed on this host's cores for a few
+    iterations.  Returns (record, counts): the counts drawn from the oracle's
+    projector serve the oracle-parity check of the GPU result."""
     oracle, cfg, g, S, mu, y, eta = oracle_inputs(cfg_name)
     oracle.solve(g, S, mu, cfg["I0"], y, eta, 1)  # warm caches / page in
     t0 = time.perf_counter()
@@ -199,7 +216,52 @@ def cpu_baseline(cfg_name: str, iters: int):
     dt = time.perf_counter() - t0
     return {"value": iters / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
             "sample": f"{iters} extragradient iterations of the same workload (counts regenerated by the oracle's "
-                      f"projector), FP64; forward projection on all OpenMP threads, scatter adjoint on one"}
+                      f"projector), FP64; forward projection on all OpenMP threads, scatter adjoint on one"}, y
+
+
+GOLDEN_C3 = os.path.join(ROOT, "tests", "golden", "c3_oracle.npz")
+
+
+def oracle_parity(ex, torch, dev, cfg_name: str, y_or):
+    """The GPU solve of the headline workload against the FP64 oracle's stored
+    iterates (tests/golden/c3_oracle.npz, written by make_c3_oracle.py from
+    the same oracle counts, step and x_1 = 0): relative L2 error and PSNR
+    difference at each stored iteration count.  None when the stored file is
+    missing or was computed with other oracle/input sources."""
+    if cfg_name != "C3" or not os.path.exists(GOLDEN_C3):
+        return None
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    try:
+        import make_c3_oracle
+    finally:
+        sys.path.pop(0)
+    data = np.load(GOLDEN_C3)
+    meta = json.loads(str(data["meta"]))
+    if meta.get("sources_sha256") != make_c3_oracle.source_digest():
+        return {"stale": "stored oracle iterates were computed from other sources"}
+    cfg, S, mu, xs, _ = workload(cfg_name)
+    plan = ex.Plan(ex.Geometry(**cfg["geometry"]), mu, S)
+    plan.autotune()
+    y = torch.as_tensor(y_or, dtype=torch.bfloat16 if cfg["y_dtype"] == "bf16" else torch.float32,
+                        device=dev).contiguous()
+    x = torch.zeros(plan.shape_img, dtype=torch.float32, device=dev)
+    out, done = {}, 0
+
+    def psnr(a):
+        return 20.0 * math.log10(1.0 / float(np.sqrt(np.mean((np.asarray(a, np.float64) - xs) ** 2))))
+
+    for t in meta["checkpoints"]:
+        plan.solve(y, meta["I0"], meta["eta"], t - done, x=x)
+        done = t
+        ref = data[f"x{t}"].astype(np.float64)
+        got = x.double().cpu().numpy()
+        out[f"iters_{t}"] = {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                             "psnr_db": psnr(got), "oracle_psnr_db": psnr(ref),
+                             "dpsnr_db": psnr(got) - psnr(ref)}
+    plan.close()
+    out["against"] = ("FP64 CPU oracle, same BF16 counts, eta and x_1 = 0 (tests/golden/c3_oracle.npz); "
+                      "bar: rel-L2 <= 1e-3, |dPSNR| <= 0.05 dB")
+    return out
 
 
 def run_reference(args):
@@ -207,6 +269,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     oracle, cfg, g, S, mu, y, eta = oracle_inputs(args.config)
+    cores = oracle.threads()
     x = np.zeros((g.ny, g.nx))
     for _ in range(args.warmup):
         x = oracle.solve(g, S, mu, cfg["I0"], y, eta, 1, x1=x).x
@@ -219,9 +282,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded random-ellipse phantom, Poisson counts)",
-            "config": {"workload": describe(cfg), "step": "one extragradient iteration of the FP64 CPU oracle",
-                       "parallelism": "host cores"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "config": bench_config(cfg, world),
+            "step": f"one extragradient iteration of the FP64 CPU oracle on {cores} host cores (a bounded sample "
+                    f"of the {cfg['iters']}-iteration solve)",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} iterations, one per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -277,7 +341,7 @@ SERVE_SCALES = {
 
 
 def run_served(ex, torch, dev, n_jobs: int, loads, rank: int, round_iters: int = 20, scale: str = "small",
-               sat_work: float = 4e8):
+               sat_work: float = 4e8, mode: str = "streams"):
     """A Poisson stream of reconstruction requests (image sizes 128..512,
     90..720 views, parallel or fan beam, 1..4 windows, 16..64 energies,
     tolerance 1e-3; scale "full": 128..1024, 90..1440 views, tolerance 1e-4)
@@ -319,9 +383,10 @@ def run_served(ex, torch, dev, n_jobs: int, loads, rank: int, round_iters: int =
             t += float(rng.exponential(1.0 / rate))
             r.arrival = t
         server = Server(budget_bytes=configs.C5["budget_bytes"], max_slots=64, round_iters=round_iters,
-                        sat_work=sat_work)
+                        sat_work=sat_work, mode=mode)
         served = summarise(server.run(reqs, realtime=True))
         served["rounds"] = server.rounds
+        served["peak_resident"] = server.peak_resident
         server.close()
         plain = summarise(serve_sequential(reqs, realtime=True))
         points.append({"load_vs_sequential_capacity": load, "arrival_rate_per_s": rate, "served": served,
@@ -330,8 +395,9 @@ def run_served(ex, torch, dev, n_jobs: int, loads, rank: int, round_iters: int =
     return {"requests": n_jobs, "sequential_capacity_per_s": cap,
             "workload": f"Poisson stream; {sc['sizes'][0]}..{sc['sizes'][1]}^2, {sc['views'][0]}..{sc['views'][1]} "
                         "views, parallel/fan 50/50, 1..4 windows, 16..64 "
-                        f"energies, tol {sc['tol']:g}, HBM budget 150 GB, {round_iters} iterations per round, "
-                        f"admission up to {sat_work:g} nonzeros of A per iteration",
+                        f"energies, tol {sc['tol']:g}, HBM budget 150 GB, admission up to {sat_work:g} nonzeros "
+                        f"of A per iteration",
+            "server_mode": mode if mode == "streams" else f"rounds of {round_iters} iterations",
             "loads": points}
 
 
@@ -617,6 +683,35 @@ def run_batched(ex, torch, dev, n_jobs: int, iters: int, rank: int):
     return out
 
 
+def batched_summary(b: dict) -> dict:
+    """The batched leg in a few keys: reconstructions/s of each form, latency,
+    PSNR, speed-up over one-at-a-time solves."""
+    s, p, g = b["sequential"], b["batched"], b["batched_graph"]
+    return {"jobs": b["jobs"], "iters": b["iters_per_job"],
+            "recon_per_s": {"sequential": round(s["recon_per_s"], 2), "batched": round(p["recon_per_s"], 2),
+                            "graph": round(g["recon_per_s"], 2)},
+            "p50_p99_ms": {"sequential": [round(s["p50_latency_ms"], 1), round(s["p99_latency_ms"], 1)],
+                           "batched": [round(p["p50_latency_ms"], 1), round(p["p99_latency_ms"], 1)]},
+            "psnr_db": {"sequential": round(s["mean_psnr_db"], 3), "batched": round(p["mean_psnr_db"], 3)},
+            "speedup": round(b["speedup_vs_sequential"], 3)}
+
+
+def served_summary(sv: dict) -> dict:
+    """The served leg in a few keys per load: reconstructions/s, p50/p99
+    latency and PSNR of the server and of one-at-a-time solves."""
+    out = {"requests": sv["requests"], "capacity_per_s": round(sv["sequential_capacity_per_s"], 3)}
+    for pt in sv["loads"]:
+        a, q = pt["served"], pt["sequential"]
+        out[f"load_{pt['load_vs_sequential_capacity']:g}"] = {
+            "recon_per_s": [round(a["recon_per_s"], 3), round(q["recon_per_s"], 3)],
+            "p50_s": [round(a["p50_latency_s"], 3), round(q["p50_latency_s"], 3)],
+            "p99_s": [round(a["p99_latency_s"], 3), round(q["p99_latency_s"], 3)],
+            "psnr_db": [round(a["mean_psnr_db"], 3), round(q["mean_psnr_db"], 3)],
+            "speedup": round(pt["speedup_recon_per_s"], 3)}
+    out["order"] = "[served, sequential]"
+    return out
+
+
 def run_exact(args):
     import torch
     import torch.distributed as dist
@@ -698,43 +793,46 @@ def run_exact(args):
     # end to end through the public API with host buffers
     y_host = y.cpu().pin_memory()
     x_host = torch.zeros(plan.shape_img, dtype=torch.float32).pin_memory()
-    y_dev = torch.empty_like(y)
-    x_dev = torch.empty_like(x)
-    plan.solve_host(y_host, I0, eta, iters, x_host, y_dev=y_dev, x_dev=x_dev)  # warm
+    plan.solve_host(y_host, I0, eta, iters, x_host)  # warm
     e2e_ms = []
     for k in range(args.steps):
         flush.fill_(float(k))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         x_host.zero_()
         a.record(stream)
-        plan.solve_host(y_host, I0, eta, iters, x_host, y_dev=y_dev, x_dev=x_dev)
+        plan.solve_host(y_host, I0, eta, iters, x_host)
         b.record(stream)
         b.synchronize()
         e2e_ms.append(a.elapsed_time(b))
     e2e_t = reduce_max(sum(e2e_ms) / 1e3, world, dev)
     e2e_value = iters * args.steps * world / e2e_t
 
-    # roofline of the dominant kernel (the adjoint gather, both epilogues)
+    # roofline of the dominant kernel (the adjoint gather, both epilogues):
+    # nonzeros per second against the measured shared-memory gather rate
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    ceiling_wps, sms = ex.gather_ceiling()
+    peak_gnnz = ceiling_wps / 1e9
+    nominal_gnnz = sms * L1_WORDS_PER_CLK * sm_max * 1e6 / 1e9
     adj_ms = prof["adjoint_half"][0] + prof["adjoint_full"][0]
     adj_n = prof["adjoint_half"][1] + prof["adjoint_full"][1]
     fwd_ms, fwd_n = prof["forward_link"]
     adj_avg = adj_ms / max(adj_n, 1)
     fwd_avg = fwd_ms / max(fwd_n, 1)
-    peak_gnnz = SMS * L1_WORDS_PER_CLK * sm_max * 1e6 / 1e9
     achieved = nnz / (adj_avg * 1e-3) / 1e9
     traffic = load_traffic("adjoint")
     hbm_gbs = float(peaks.get("hbm_gbs", 6686.1))
     roof = {"bound": "alu", "kernel": "k_adjoint (pixel-driven gather + extragradient epilogue)",
             "achieved": achieved, "peak": peak_gnnz, "unit": "Gnnz/s", "frac": achieved / peak_gnnz,
             "traffic": traffic["dram_bytes"] if traffic else None,
-            "peak_source": f"{SMS} SMs x {L1_WORDS_PER_CLK} FP32 words/clk (128 B/clk L1 path) x "
-                           f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+            "peak_source": f"measured: exact_probe_gather_ceiling (conflict-free 4-byte shared loads on all {sms} "
+                           f"SMs, CUDA events) = {peak_gnnz:.0f} G words/s; nominal {sms} SMs x {L1_WORDS_PER_CLK} "
+                           f"words/clk x {sm_max:.0f} MHz = {nominal_gnnz:.0f}",
+            "peak_nominal": nominal_gnnz, "frac_of_nominal": achieved / nominal_gnnz,
             "avg_launch_ms": adj_avg, "nnz_per_launch": nnz,
             "forward": {"avg_launch_ms": fwd_avg, "achieved": nnz / (fwd_avg * 1e-3) / 1e9,
                         "frac": nnz / (fwd_avg * 1e-3) / 1e9 / peak_gnnz},
@@ -749,30 +847,38 @@ def run_exact(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded random-ellipse phantom; Poisson counts from this path's projector)",
-            "config": {"workload": describe(cfg), "iters_per_step": iters, "step": "one exact_solve call",
-                       "l2": "flushed before every step (256 MiB write outside the timed events)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": bench_config(cfg, world),
+            "step": f"one exact_solve call of {iters} iterations",
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": y.numel() * y.element_size()
-                    + x.numel() * 4, "d2h_bytes_per_step": x.numel() * 4},
+                    + x.numel() * 4, "d2h_bytes_per_step": x.numel() * 4,
+                    "path": "exact_solve_host (C ABI: host counts and x_1 in, image out, copies inside the call)"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks.summary(),
             "psnr_db": psnr, "eta": eta, "normA_sq": normA, "norm_estimate": {"ms": norm_ms, "iters": norm_iters},
             "plan_create_ms": plan_ms, "tuning": {**tuning, "autotune_ms": tune_ms}}
-    if not args.no_batched:
-        line["batched"] = run_batched(ex, torch, dev, args.batch_jobs, args.batch_iters or configs.C4["iters"], rank)
-    if not args.no_served:
-        line["served"] = run_served(ex, torch, dev, args.serve_jobs,
-                                    [float(v) for v in args.serve_loads.split(",") if v], rank,
-                                    args.serve_round_iters, args.serve_scale, args.serve_sat_work)
+    # verbose legs first; the compact summaries the headline needs go last
+    batched = served = None
     if not args.no_tv:
         line["tv"] = run_tv(ex, torch, dev, rank)
     if not args.no_gaussian:
         line["gaussian"] = run_gaussian(ex, torch, dev)
     if not args.no_extensions:
         line["extensions"] = run_extensions(ex, torch, dev, rank)
+    if not args.no_batched:
+        batched = run_batched(ex, torch, dev, args.batch_jobs, args.batch_iters or configs.C4["iters"], rank)
+        line["batched_detail"] = batched
+    if not args.no_served:
+        served = run_served(ex, torch, dev, args.serve_jobs, [float(v) for v in args.serve_loads.split(",") if v],
+                            rank, args.serve_round_iters, args.serve_scale, args.serve_sat_work, args.serve_mode)
+        line["served_detail"] = served
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_baseline_iters)
+        line["cpu_baseline"], y_or = cpu_baseline(args.config, args.cpu_baseline_iters)
+        line["oracle_parity"] = oracle_parity(ex, torch, dev, args.config, y_or)
+    if batched is not None:
+        line["batched"] = batched_summary(batched)
+    if served is not None:
+        line["served"] = served_summary(served)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

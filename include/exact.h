@@ -129,8 +129,12 @@ exact_status exact_plan_bind_workspace(exact_plan_t plan, void *dev_ptr, size_t 
  * Needs the workspace. */
 exact_status exact_forward(exact_plan_t plan, const float *x, float *z, exact_stream_t stream);
 
-/* g = A^T r, the exact transpose of exact_forward's matrix, evaluated as a
- * deterministic pixel-driven gather (fixed order, no atomics).
+/* g = A^T r for the matrix of exact_forward, evaluated as a deterministic
+ * pixel-driven gather (fixed order, no atomics).  Both calls evaluate the
+ * same entries delta_i max(0, 1 - |t_i(j) - k|), but the FP32 route to the
+ * crossing t_i(j) differs (exact_forward anchors it per ray and per group of
+ * driving lines, this call steps it from a neighbouring ray), so the two are
+ * transposes of each other up to ~1e-6 pixel in t and FP32 summation order.
  * r: device [n_views][n_bins] FP32; g: device [ny][nx] FP32.  No workspace. */
 exact_status exact_adjoint(exact_plan_t plan, const float *r, float *g, exact_stream_t stream);
 
@@ -286,7 +290,31 @@ typedef struct {
     double tv_bound; /* > 0: X = {||x||_TV <= tv_bound} ∩ [lo, hi]^d (see exact_tv_project) */
     exact_tv_opts tv; /* options of that projection */
     double prox_lambda; /* > 0: the proximal variant of the Discussion (see below) */
+    /* Checkpoint / resume (no counterpart in the paper: the iteration of
+     * Eq. (11) only needs x_t, plus the averaging sums and the TV bisection's
+     * lam pair when those are in use).  The call runs iterations
+     * t0 + 1 .. t0 + iters; with t0 > 0, x holds the last iterate of the call
+     * that ran up to t0 (its x_last), and the averaging sums and lam pair are
+     * continued from `resume` instead of being started afresh, so the iterates,
+     * averages, stopping tests and info.iters_done (a total) are bitwise those
+     * of one call of t0 + iters iterations, provided nothing else used that
+     * state in between. */
+    int t0;          /* iterations run by earlier calls of this solve (0: a fresh solve) */
+    int total_iters; /* iterations of the whole solve, for average_tail's window (0: t0 + iters) */
+    void *resume;    /* device, exact_solve_resume_bytes(plan) bytes, 8-byte aligned, caller-owned:
+                      * the averaging sums and lam pair; NULL: kept in the workspace */
+    float *x_last;   /* device [ny][nx] or NULL: receives the last iterate (x receives the average
+                      * when an averaging option is on) */
+    int launch;      /* 0: one CUDA graph whose WHILE node loops over the iterations on the device
+                      * (the stopping test ends the loop; no launch runs after a stop) whenever the
+                      * stream is not capturing, profiling is off and there is no TV ball or
+                      * proximal step, else one stream launch per kernel; 1: always the latter */
+    int pad;
 } exact_solve_opts;
+
+/* Bytes of the caller-owned resume state of exact_solve_opts.resume:
+ * 8 (nx ny + 2). */
+size_t exact_solve_resume_bytes(exact_plan_t plan);
 
 typedef struct {
     int iters_done;      /* iterations run */
@@ -298,7 +326,8 @@ typedef struct {
 
 /* Default options: lo = 0, hi = +inf, tol = 0, check_every = 1, average_tail = 0,
  * stop_rule = EXACT_STOP_RESIDUAL, no history, tv_bound = 0 (no TV ball),
- * tv = exact_tv_opts_default(), prox_lambda = 0. */
+ * tv = exact_tv_opts_default(), prox_lambda = 0, t0 = 0, total_iters = 0,
+ * resume = NULL, x_last = NULL, launch = 0. */
 exact_solve_opts exact_solve_opts_default(void);
 
 /* Projected extragradient, Eq. (11), with constant step eta:
@@ -307,10 +336,25 @@ exact_solve_opts exact_solve_opts_default(void);
  * on entry (projected onto X first) and the result on return; info: host
  * struct written once the stream reaches the end of the solve (valid after
  * synchronising the stream), may be NULL; opts NULL means the defaults.
- * Needs the workspace. */
+ * Needs the workspace.  With opts.launch = 0 the plan keeps up to four
+ * instantiated CUDA graphs, keyed by the kernel arguments that do not change
+ * between calls of one reconstruction (I0, eta, bounds, averaging buffers,
+ * split), so repeated calls (rounds of a server, resumed solves) relaunch one
+ * graph; a new key may wait for the oldest graph's last launch to finish. */
 exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, double I0, double eta,
                          int iters, const exact_solve_opts *opts, float *x, exact_solve_info *info,
                          exact_stream_t stream);
+
+/* exact_solve from host memory: copies the counts y_host ([n_windows][n_views]
+ * [n_bins] of type y_dtype) and x_1 from x_host ([ny][nx] FP32) into the
+ * plan's workspace, runs exact_solve there and copies the result back into
+ * x_host, all on `stream`, then synchronises it (so info is valid on return).
+ * Host buffers may be pageable or pinned (pinned copies run at full bus
+ * speed).  Not allowed while `stream` is being captured
+ * (EXACT_ERR_UNSUPPORTED).  Needs the workspace. */
+exact_status exact_solve_host(exact_plan_t plan, const void *y_host, exact_dtype y_dtype, double I0, double eta,
+                              int iters, const exact_solve_opts *opts, float *x_host, exact_solve_info *info,
+                              exact_stream_t stream);
 
 /* ||A||_op^2 = lambda_max(A^T A) by FP64 power iteration on the device
  * (Sec. 4.2 needs lambda_max(Sigma) = ||A||^2 / n for the step size of
@@ -334,7 +378,7 @@ exact_status exact_norm_estimate_f32(exact_plan_t plan, int max_iters, double rt
  * (the Lipschitz bound of Sec. 4.2, m = n_windows * n_rays).  Host arithmetic. */
 exact_status exact_recommended_eta(exact_plan_t plan, double I0, double normA_sq, double *eta);
 
-/* F(x) exactly as exact_operator computes it, for callers that cannot
+/* F(x) as exact_operator computes it, for callers that cannot
  * allocate device memory when they need it: allocator-free real-time loops
  * that must not stall on cudaMalloc, and processes whose device memory is
  * owned by another framework's pool and cannot spare a separate workspace.  The paper has no counterpart: this is a
@@ -348,7 +392,11 @@ exact_status exact_recommended_eta(exact_plan_t plan, double I0, double normA_sq
  *    rejected with EXACT_ERR_UNSUPPORTED.
  *  - The first call on a device looks the array's device address up (with that
  *    device current) and keeps it; make that first call before any stream
- *    capture.
+ *    capture.  cudaDeviceReset invalidates the kept address: do not call this
+ *    entry point again in a process that reset the device.
+ *  - The adjoint runs one CTA per 16 x 16 tile whatever the plan's
+ *    exact_tuning.adj_split (a split needs the workspace), so F equals
+ *    exact_operator's up to the FP32 summation order when adj_split > 1.
  *  - Every call shares the array and it keeps the last call's contents (each
  *    call writes all scratch it reads, so nothing has to be cleared); calls
  *    that overlap on the GPU -- other streams, other threads -- race on it.
@@ -439,6 +487,15 @@ exact_status exact_profile_enable(exact_plan_t plan, int sample_every);
  * them.  Either array may be NULL. */
 exact_status exact_profile_read(exact_plan_t plan, double ms[EXACT_PROF_KINDS],
                                 long long launches[EXACT_PROF_KINDS]);
+
+/* Measurement aid (no counterpart in the paper): the rate, in 4-byte words per
+ * second, at which the current device serves bank-conflict-free shared-memory
+ * loads, measured by a kernel that issues only such loads on every SM (one full
+ * wave, best of five launches timed with CUDA events on `stream`).  The
+ * projector kernels gather one such operand per nonzero of A, so nonzeros per
+ * second over this rate is their fraction of the on-chip gather ceiling.
+ * sm_count (may be NULL) receives the device's SM count.  Synchronises. */
+exact_status exact_probe_gather_ceiling(double *words_per_s, int *sm_count, exact_stream_t stream);
 
 /* Static description of a status code. */
 const char *exact_status_string(exact_status status);

@@ -271,29 +271,6 @@ bool build_units(const exact_geometry &g, const std::vector<RayF> &rf, const std
     return true;
 }
 
-// Encodes the 2D tensor map (x = padded cross index, y = driving line) of one
-// padded image copy; box kFHB x kFC, zero fill outside.
-bool encode_map(CUtensorMap *map, float *base, long long ld, long long lines)
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        cudaDriverEntryPointQueryResult q;
-        void *ptr = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !ptr)
-            return false;
-        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-    }
-    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)lines};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)kFHB, (cuuint32_t)kFC};
-    const cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 ViewRec make_view(const exact_geometry &g, int v, int xb0, int xb1, int yb0, int yb1)
 {
     const double th = g.angle0 + (double)v * g.angle_range / (double)g.n_views;
@@ -387,6 +364,8 @@ size_t carve(Plan &P, char *base)
     P.tv_step = c.take<float>(base, (size_t)P.d);
     P.tv_lam = c.take<double>(base, 2);
     if (P.tv_grid > 0) P.tv_ws = c.take<char>(base, tv_workspace_bytes(nx, ny, P.tv_grid));
+    P.stage_y = c.take<float>(base, (size_t)P.W * (size_t)P.n);  // host-buffer solve: counts (FP32 or BF16)
+    P.stage_x = c.take<float>(base, (size_t)P.d);                // and the image
     return c.off;
 }
 
@@ -428,18 +407,6 @@ exact_status enqueue_info(DevState *st, DevState *host_state, exact_solve_info *
     return EXACT_OK;
 }
 
-LinkCoef make_coef(const Plan &P, double I0)
-{
-    LinkCoef c;
-    memset(&c, 0, sizeof(c));
-    for (int k = 0; k < P.K; ++k) {
-        c.mu2[k] = P.mu_log2e[k];
-        c.c[k] = (float)(I0 * (double)P.C[k]);
-        for (int m = 0; m < P.bg_M; ++m) c.mub[m][k] = P.bg_mu2[m][k];
-    }
-    return c;
-}
-
 ImgF img_of(const Plan &P, int q)
 {
     ImgF im;
@@ -466,6 +433,127 @@ int prof_begin(Plan &P, int kind, int iter, cudaStream_t s)
 void prof_end(Plan &P, int u, cudaStream_t s)
 {
     if (u >= 0) cudaEventRecord(P.prof_ev[2 * u + 1], s);
+}
+
+// View split of a new plan's adjoint, before any autotuning: the largest of
+// {1, 2, 3, 4, 6, 8} that keeps tiles x split within about 27 CTAs per SM
+// (four waves of the 7 adjoint CTAs resident per SM).  Small images get more
+// CTAs than they have tiles; the 512^2 images of the headline workload get 4,
+// which is what the autotuner measures best there.
+int default_split(const Plan &P)
+{
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P.device) != cudaSuccess || sms <= 0) sms = 1;
+    const long long tiles = adjoint_blocks(P.g.nx, P.g.ny), want = 27LL * sms;
+    int best = 1;
+    for (int s : {1, 2, 3, 4, 6, 8})
+        if (tiles * s <= want) best = s;
+    return best;
+}
+
+void free_solve_graphs(Plan &P)
+{
+    for (SolveGraph &g : P.graphs) {
+        if (g.last) {
+            cudaEventSynchronize(g.last);
+            cudaEventDestroy(g.last);
+        }
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    }
+    P.graphs.clear();
+    if (P.cap_stream) cudaStreamDestroy(P.cap_stream);
+    P.cap_stream = nullptr;
+}
+
+// Runs a solve's iterations as one CUDA graph launch on s: the graph is a
+// single WHILE node whose body holds one iteration's kernels, captured from
+// body(cond, stream) on the plan's capture stream; the body's reduction
+// kernel sets the loop condition, so the loop stops on the device after the
+// stopping test passes or the last iteration.  The instantiated graph is kept
+// under `key` (the kernel arguments that the device state does not supply)
+// and relaunched when the key recurs; with kSolveGraphs kept, a new one
+// replaces the least recently used after that one's last launch has finished.
+template <typename Body>
+exact_status launch_solve_graph(Plan &P, const void *key, size_t key_bytes, Body &&body, cudaStream_t s)
+{
+    const unsigned char *kb = static_cast<const unsigned char *>(key);
+    SolveGraph *hit = nullptr;
+    for (SolveGraph &g : P.graphs)
+        if (g.key.size() == key_bytes && memcmp(g.key.data(), kb, key_bytes) == 0) {
+            hit = &g;
+            break;
+        }
+    if (!hit) {
+        if (!P.cap_stream) EXACT_TRY(cudaStreamCreateWithFlags(&P.cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        EXACT_TRY(cudaGraphCreate(&graph, 0));
+        exact_status st = EXACT_OK;
+        cudaGraphExec_t exec = nullptr;
+        cudaEvent_t last = nullptr;
+        do {
+            cudaGraphConditionalHandle cond = 0;
+            cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault);
+            if (e != cudaSuccess) {
+                st = cuda_status(e);
+                break;
+            }
+            // zeroed storage: the struct's union has no default constructor
+            alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)] = {};
+            cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(np_raw);
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = cond;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node = nullptr;
+            if ((e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np)) != cudaSuccess) {
+                st = cuda_status(e);
+                break;
+            }
+            cudaGraph_t loop = np.conditional.phGraph_out[0];
+            if ((e = cudaStreamBeginCaptureToGraph(P.cap_stream, loop, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeRelaxed)) != cudaSuccess) {
+                st = cuda_status(e);
+                break;
+            }
+            st = body(cond, P.cap_stream);
+            cudaGraph_t captured = nullptr;
+            e = cudaStreamEndCapture(P.cap_stream, &captured);
+            if (st == EXACT_OK && e != cudaSuccess) st = cuda_status(e);
+            if (st != EXACT_OK) break;
+            if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) {
+                exec = nullptr;
+                st = cuda_status(e);
+                break;
+            }
+            if ((e = cudaEventCreateWithFlags(&last, cudaEventDisableTiming)) != cudaSuccess) {
+                st = cuda_status(e);
+                break;
+            }
+        } while (0);
+        cudaGraphDestroy(graph);
+        if (st != EXACT_OK) {
+            if (exec) cudaGraphExecDestroy(exec);
+            return st;
+        }
+        if ((int)P.graphs.size() >= kSolveGraphs) {
+            auto lru = std::min_element(P.graphs.begin(), P.graphs.end(),
+                                        [](const SolveGraph &u, const SolveGraph &v) { return u.stamp < v.stamp; });
+            cudaEventSynchronize(lru->last);
+            cudaEventDestroy(lru->last);
+            cudaGraphExecDestroy(lru->exec);
+            P.graphs.erase(lru);
+        }
+        SolveGraph g;
+        g.exec = exec;
+        g.last = last;
+        g.key.assign(kb, kb + key_bytes);
+        P.graphs.push_back(std::move(g));
+        hit = &P.graphs.back();
+    }
+    hit->stamp = ++P.graph_clock;
+    EXACT_TRY(cudaGraphLaunch(hit->exec, s));
+    EXACT_TRY(cudaEventRecord(hit->last, s));
+    return EXACT_OK;
 }
 
 void prof_free(Plan &P)
@@ -498,6 +586,46 @@ long long count_nnz(const exact_geometry &g)
 
 }  // namespace
 
+namespace exact {
+
+// Encodes the 2D tensor map (x = padded cross index, y = driving line) of one
+// padded image copy; box kFHB x kFC, zero fill outside.  The driver entry
+// point is looked up once per process (thread-safe static initialisation).
+bool encode_map(CUtensorMap *map, float *base, long long ld, long long lines)
+{
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        cudaDriverEntryPointQueryResult q;
+        void *ptr = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)lines};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kFHB, (cuuint32_t)kFC};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+LinkCoef make_coef(const Plan &P, double I0)
+{
+    LinkCoef c;
+    memset(&c, 0, sizeof(c));
+    for (int k = 0; k < P.K; ++k) {
+        c.mu2[k] = P.mu_log2e[k];
+        c.c[k] = (float)(I0 * (double)P.C[k]);
+        for (int m = 0; m < P.bg_M; ++m) c.mub[m][k] = P.bg_mu2[m][k];
+    }
+    return c;
+}
+
+}  // namespace exact
+
 extern "C" {
 
 const char *exact_status_string(exact_status s)
@@ -529,7 +657,19 @@ exact_solve_opts exact_solve_opts_default(void)
     o.tv_bound = 0.0;
     o.tv = exact_tv_opts_default();
     o.prox_lambda = 0.0;
+    o.t0 = 0;
+    o.total_iters = 0;
+    o.resume = nullptr;
+    o.x_last = nullptr;
+    o.launch = 0;
+    o.pad = 0;
     return o;
+}
+
+size_t exact_solve_resume_bytes(exact_plan_t plan)
+{
+    if (!plan) return 0;
+    return sizeof(double) * (size_t)(reinterpret_cast<Plan *>(plan)->d + 2);
 }
 
 exact_status exact_plan_create(const exact_geometry *geometry, const exact_spectrum *spectrum,
@@ -634,28 +774,41 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
     }
     if (kst.empty()) kst.push_back(0);
     P->n_units = (int)units.size();
-    cudaError_t e = cudaMalloc(&P->rays_f, sizeof(RayF) * rf.size());
+    // uploads on a private non-blocking stream: a plan built on one host
+    // thread does not wait for (or hold up) work that other threads run on
+    // the legacy default stream
+    cudaStream_t up = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking);
+    auto put = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, up);
+    };
+    if (e == cudaSuccess) e = cudaMalloc(&P->rays_f, sizeof(RayF) * rf.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->rays_w, sizeof(RayW) * rw.size());
-    if (e == cudaSuccess) e = cudaMemcpy(P->rays_w, rw.data(), sizeof(RayW) * rw.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&P->units, sizeof(FwdUnit) * units.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->kstart, sizeof(int) * kst.size());
-    if (e == cudaSuccess) e = cudaMemcpy(P->units, units.data(), sizeof(FwdUnit) * units.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->kstart, kst.data(), sizeof(int) * kst.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&P->ray_bits, sizeof(int) * rbits.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->ray_delta, sizeof(float) * rdelta.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->rays_d, sizeof(RayD) * rd.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->views, sizeof(ViewRec) * vw.size());
-    if (e == cudaSuccess) e = cudaMemcpy(P->rays_f, rf.data(), sizeof(RayF) * rf.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->ray_bits, rbits.data(), sizeof(int) * rbits.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(P->ray_delta, rdelta.data(), sizeof(float) * rdelta.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->rays_d, rd.data(), sizeof(RayD) * rd.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(P->views, vw.data(), sizeof(ViewRec) * vw.size(), cudaMemcpyHostToDevice);
+    put(P->rays_w, rw.data(), sizeof(RayW) * rw.size());
+    put(P->units, units.data(), sizeof(FwdUnit) * units.size());
+    put(P->kstart, kst.data(), sizeof(int) * kst.size());
+    put(P->rays_f, rf.data(), sizeof(RayF) * rf.size());
+    put(P->ray_bits, rbits.data(), sizeof(int) * rbits.size());
+    put(P->ray_delta, rdelta.data(), sizeof(float) * rdelta.size());
+    put(P->rays_d, rd.data(), sizeof(RayD) * rd.size());
+    put(P->views, vw.data(), sizeof(ViewRec) * vw.size());
+    if (up) {
+        const cudaError_t es = cudaStreamSynchronize(up);  // the host vectors die at return
+        if (e == cudaSuccess) e = es;
+        cudaStreamDestroy(up);
+    }
     if (e == cudaSuccess) e = cudaMallocHost(&P->host_state, sizeof(DevState));
     if (e != cudaSuccess) {
         exact_plan_destroy(reinterpret_cast<exact_plan_t>(P));
         return cuda_status(e);
     }
+    P->adj_split = default_split(*P);
     memset(P->host_state, 0, sizeof(DevState));
     *out = reinterpret_cast<exact_plan_t>(P);
     return EXACT_OK;
@@ -676,6 +829,7 @@ exact_status exact_plan_destroy(exact_plan_t plan)
     if (P->ray_delta) cudaFree(P->ray_delta);
     if (P->rays_d) cudaFree(P->rays_d);
     if (P->views) cudaFree(P->views);
+    free_solve_graphs(*P);
     if (P->host_state) cudaFreeHost(P->host_state);
     if (P->prof_ev) prof_free(*P);
     for (void *c : P->captured_infos) delete static_cast<InfoCopy *>(c);
@@ -704,6 +858,7 @@ exact_status exact_plan_bind_workspace(exact_plan_t plan, void *dev_ptr, size_t 
 {
     if (!plan) return EXACT_ERR_INVALID_ARG;
     Plan *P = reinterpret_cast<Plan *>(plan);
+    free_solve_graphs(*P);  // they hold pointers into the old workspace
     if (!dev_ptr) {
         P->ws = nullptr;
         P->ws_bytes = 0;
@@ -961,8 +1116,14 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
         return EXACT_ERR_INVALID_ARG;
     if (!isfin(o.tol) || o.tol < 0.0 || o.check_every < 0) return EXACT_ERR_INVALID_ARG;
     if (o.stop_rule != EXACT_STOP_RESIDUAL && o.stop_rule != EXACT_STOP_AVERAGE) return EXACT_ERR_INVALID_ARG;
+    if (o.t0 < 0 || o.total_iters < 0 || (long long)o.t0 + iters > INT_MAX / 2) return EXACT_ERR_INVALID_ARG;
+    if (o.launch != 0 && o.launch != 1) return EXACT_ERR_INVALID_ARG;
+    if (o.resume && (reinterpret_cast<uintptr_t>(o.resume) & 7u)) return EXACT_ERR_INVALID_ARG;
+    const int t0 = o.t0, t_end = o.t0 + iters;
+    const int T = o.total_iters > 0 ? o.total_iters : t_end;
+    if (T < t_end) return EXACT_ERR_INVALID_ARG;
     const bool running = o.stop_rule == EXACT_STOP_AVERAGE;
-    if (running && (o.average_tail || !o.history || o.history_cap < (iters / 2 > 1 ? iters / 2 : 1)))
+    if (running && (o.average_tail || !o.history || o.history_cap < (t_end / 2 > 1 ? t_end / 2 : 1)))
         return EXACT_ERR_INVALID_ARG;
     if (isnan(o.tv_bound) || o.tv_bound < 0.0 || o.tv_bound == INFINITY) return EXACT_ERR_INVALID_ARG;
     if (isnan(o.prox_lambda) || o.prox_lambda < 0.0 || o.prox_lambda == INFINITY) return EXACT_ERR_INVALID_ARG;
@@ -976,23 +1137,32 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     Plan &P = *reinterpret_cast<Plan *>(plan);
     if (tvb && !P.tv_ws) return EXACT_ERR_CUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    EXACT_TRY(cudaStreamIsCapturing(s, &cap));
     const float lo = (float)o.lo, hi = (float)o.hi;
     const LinkCoef coef = make_coef(P, I0);
-    const int avg_from = iters / 2;
+    const int avg_from = T / 2;
     const int nb = adjoint_blocks(P.g.nx, P.g.ny);
+    const bool averaging = o.average_tail || running;
+    // state continued across calls of one solve: the averaging sums [d] and
+    // the lam pair of the TV projections
+    double *avg = o.resume ? static_cast<double *>(o.resume) : P.avg;
+    double *tv_lam = o.resume ? static_cast<double *>(o.resume) + P.d : P.tv_lam;
 
-    EXACT_TRY(launch_reset_state(P.state, s));
+    EXACT_TRY(launch_reset_state(P.state, t0, t_end, o.tol, o.check_every, o.stop_rule, avg_from, s));
     EXACT_TRY(reset_split_counts(P, s));
     EXACT_TRY(launch_collapse(y, y_dtype, P.W, P.n, P.Y, s));
     EXACT_TRY(launch_pack(x, P.xr[0], P.xc[0], P.g.nx, P.g.ny, P.ldr(), P.ldc(), lo, hi, true, s));
     EXACT_TRY(cudaMemsetAsync(P.xr[1], 0, sizeof(float) * (size_t)(P.g.ny * P.ldr()), s));
     EXACT_TRY(cudaMemsetAsync(P.xc[1], 0, sizeof(float) * (size_t)(P.g.nx * P.ldc()), s));
-    if (o.average_tail || running) EXACT_TRY(cudaMemsetAsync(P.avg, 0, sizeof(double) * (size_t)P.d, s));
+    if (averaging && t0 == 0) EXACT_TRY(cudaMemsetAsync(avg, 0, sizeof(double) * (size_t)P.d, s));
     TvLaunch tvl;
     memset(&tvl, 0, sizeof(tvl));
     if (tvb) {
-        const double lam2[2] = {proxm ? o.prox_lambda : o.tv.lam0, proxm ? o.prox_lambda : o.tv.lam0};
-        EXACT_TRY(cudaMemcpyAsync(P.tv_lam, lam2, sizeof(lam2), cudaMemcpyHostToDevice, s));
+        if (t0 == 0) {
+            const double lam2[2] = {proxm ? o.prox_lambda : o.tv.lam0, proxm ? o.prox_lambda : o.tv.lam0};
+            EXACT_TRY(cudaMemcpyAsync(tv_lam, lam2, sizeof(lam2), cudaMemcpyHostToDevice, s));
+        }
         tvl.nx = P.g.nx;
         tvl.ny = P.g.ny;
         tvl.grid = P.tv_grid;
@@ -1048,45 +1218,50 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     a.lo = lo;
     a.hi = hi;
     a.partials = P.partials;
-    a.avg = (o.average_tail || running) ? P.avg : nullptr;
+    a.avg = averaging ? avg : nullptr;
     a.avg_from = avg_from;
     a.state = P.state;
     a.hist = running ? o.history : nullptr;
+    a.hist_cap = o.history_cap;
     a.hist_drop = -1;
     const bool fan = P.g.beam == 1;
-    int u;
-    for (int t = 0; t < iters; ++t) {
-        // half step: x_{t+1/2} = P(x_t - eta F(x_t))
+
+    // One iteration (Eq. (11)): forward+link on x_t, half step into x_{t+1/2},
+    // forward+link on x_{t+1/2}, full step from x_t, FP64 stopping reduction.
+    // in_graph: captured into a CUDA graph loop, where the iteration index
+    // comes from the device state and the reduction sets the loop condition.
+    auto iteration = [&](int t, bool in_graph, cudaGraphConditionalHandle cond, cudaStream_t q) -> exact_status {
+        int u;
+        a.iter_from_state = in_graph ? 1 : 0;
         f.img = img_of(P, 0);
-        u = prof_begin(P, 0, t, s);
-        EXACT_TRY(launch_forward(f, true, &coef, P.maps_r[0], P.maps_c[0], s));
-        prof_end(P, u, s);
+        u = in_graph ? -1 : prof_begin(P, 0, t, q);
+        EXACT_TRY(launch_forward(f, true, &coef, P.maps_r[0], P.maps_c[0], q));
+        prof_end(P, u, q);
         a.out_r = P.xr[1];
         a.out_c = P.xc[1];
         a.iter = t;
-        u = prof_begin(P, 1, t, s);
+        u = in_graph ? -1 : prof_begin(P, 1, t, q);
         if (tvb) {
             // unprojected half step, then its projection onto the TV ball ∩ box
             a.out = P.tv_step;
-            EXACT_TRY(launch_adjoint(a, ADJ_STEP, fan, s));
+            EXACT_TRY(launch_adjoint(a, ADJ_STEP, fan, q));
             tvl.out_r = P.xr[1];
             tvl.out_c = P.xc[1];
             tvl.old_r = nullptr;
             tvl.hist = nullptr;
-            tvl.lam_io = P.tv_lam;
-            EXACT_TRY(launch_tv_project(tvl, s));
+            tvl.lam_io = tv_lam;
+            EXACT_TRY(launch_tv_project(tvl, q));
         } else {
-            EXACT_TRY(launch_adjoint(a, ADJ_EG, fan, s));
+            EXACT_TRY(launch_adjoint(a, ADJ_EG, fan, q));
         }
-        prof_end(P, u, s);
-        // full step from the same base: x_{t+1} = P(x_t - eta F(x_{t+1/2}))
+        prof_end(P, u, q);
         f.img = img_of(P, 1);
-        u = prof_begin(P, 0, t, s);
-        EXACT_TRY(launch_forward(f, true, &coef, P.maps_r[1], P.maps_c[1], s));
-        prof_end(P, u, s);
+        u = in_graph ? -1 : prof_begin(P, 0, t, q);
+        EXACT_TRY(launch_forward(f, true, &coef, P.maps_r[1], P.maps_c[1], q));
+        prof_end(P, u, q);
         a.out_r = P.xr[0];
         a.out_c = P.xc[0];
-        if (running) {
+        if (running && !in_graph) {
             // iterate number it = t + 1 enters the window of the last
             // m = max(1, floor(it/2)); when m did not grow, x_{it-m} leaves it
             const int it = t + 1, m = it / 2 > 1 ? it / 2 : 1, mp = (it - 1) / 2 > 1 ? (it - 1) / 2 : 1;
@@ -1095,39 +1270,108 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
             a.inv_m = 1.0 / (double)m;
             a.inv_m_prev = it >= 2 ? 1.0 / (double)mp : 0.0;
         }
-        u = prof_begin(P, 2, t, s);
+        u = in_graph ? -1 : prof_begin(P, 2, t, q);
         if (tvb) {
             // unprojected full step from x_t, projected into x_t's padded
             // copies (each pixel's old value is read first for the norms)
             a.out = P.tv_step;
-            EXACT_TRY(launch_adjoint(a, ADJ_STEP, fan, s));
+            EXACT_TRY(launch_adjoint(a, ADJ_STEP, fan, q));
             tvl.out_r = P.xr[0];
             tvl.out_c = P.xc[0];
             tvl.old_r = P.xr[0];
             tvl.norm_part = P.partials;
-            tvl.lam_io = P.tv_lam + 1;
+            tvl.lam_io = tv_lam + 1;
             tvl.avg = a.avg;
             tvl.hist = a.hist;
             tvl.hist_put = a.hist_put;
             tvl.hist_drop = a.hist_drop;
             tvl.inv_m = a.inv_m;
             tvl.inv_m_prev = a.inv_m_prev;
-            EXACT_TRY(launch_tv_project(tvl, s));
+            EXACT_TRY(launch_tv_project(tvl, q));
         } else {
-            EXACT_TRY(launch_adjoint(a, ADJ_EG_FINAL, fan, s));
+            EXACT_TRY(launch_adjoint(a, ADJ_EG_FINAL, fan, q));
         }
-        prof_end(P, u, s);
-        u = prof_begin(P, 3, t, s);
-        EXACT_TRY(launch_solve_reduce(P.partials, tvb ? P.tv_grid : nb, P.state, t, o.tol, o.check_every,
-                                      o.stop_rule, s));
-        prof_end(P, u, s);
+        prof_end(P, u, q);
+        u = in_graph ? -1 : prof_begin(P, 3, t, q);
+        if (in_graph)
+            EXACT_TRY(launch_solve_reduce_cond(P.partials, nb, P.state, cond, q));
+        else
+            EXACT_TRY(launch_solve_reduce(P.partials, tvb ? P.tv_grid : nb, P.state, t, q));
+        prof_end(P, u, q);
+        return EXACT_OK;
+    };
+
+    const bool use_graph =
+        iters > 0 && o.launch == 0 && !tvb && P.prof_every <= 0 && cap == cudaStreamCaptureStatusNone;
+    if (use_graph) {
+        // everything the loop's kernels take as arguments, except what they
+        // read from the device state (iteration index, stopping test, bounds)
+        struct Key {
+            LinkCoef coef;
+            float scale, lo, hi;
+            int nsplit, fan, running, averaging, hist_cap, bg_M, pad;
+            const void *avg, *hist, *bg_p;
+        } key;
+        memset(&key, 0, sizeof(key));
+        key.coef = coef;
+        key.scale = a.scale;
+        key.lo = lo;
+        key.hi = hi;
+        key.nsplit = a.nsplit;
+        key.fan = fan;
+        key.running = running;
+        key.averaging = averaging;
+        key.hist_cap = o.history_cap;
+        key.bg_M = P.bg_M;
+        key.avg = a.avg;
+        key.hist = a.hist;
+        key.bg_p = P.bg_p;
+        st = launch_solve_graph(P, &key, sizeof(key),
+                                [&](cudaGraphConditionalHandle cond, cudaStream_t q) {
+                                    return iteration(t0, true, cond, q);
+                                },
+                                s);
+        if (st != EXACT_OK) return st;
+    } else {
+        for (int t = t0; t < t_end; ++t) {
+            st = iteration(t, false, cudaGraphConditionalHandle{}, s);
+            if (st != EXACT_OK) return st;
+        }
     }
-    EXACT_TRY(launch_unpack(P.xr[0], P.ldr(), P.g.nx, P.g.ny, x, (o.average_tail || running) ? P.avg : nullptr,
-                            P.state, running ? -1 : avg_from, s));
+    EXACT_TRY(launch_unpack(P.xr[0], P.ldr(), P.g.nx, P.g.ny, x, averaging ? avg : nullptr, P.state,
+                            running ? -1 : avg_from, s));
+    if (o.x_last) EXACT_TRY(launch_unpack(P.xr[0], P.ldr(), P.g.nx, P.g.ny, o.x_last, nullptr, P.state, 0, s));
     if (info) {
         st = enqueue_info(P.state, P.host_state, info, P.captured_infos, s);
         if (st != EXACT_OK) return st;
     }
+    return EXACT_OK;
+}
+
+exact_status exact_solve_host(exact_plan_t plan, const void *y_host, exact_dtype y_dtype, double I0, double eta,
+                              int iters, const exact_solve_opts *opts, float *x_host, exact_solve_info *info,
+                              exact_stream_t stream)
+{
+    exact_status st = check_plan(plan, true);
+    if (st != EXACT_OK) return st;
+    if (!y_host || !x_host) return EXACT_ERR_INVALID_ARG;
+    if (y_dtype != EXACT_F32 && y_dtype != EXACT_BF16) return EXACT_ERR_INVALID_ARG;
+    Plan &P = *reinterpret_cast<Plan *>(plan);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    EXACT_TRY(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return EXACT_ERR_UNSUPPORTED;  // it synchronises
+    const size_t ybytes = (size_t)P.W * (size_t)P.n * (y_dtype == EXACT_BF16 ? 2 : 4);
+    const size_t xbytes = sizeof(float) * (size_t)P.d;
+    EXACT_TRY(cudaMemcpyAsync(P.stage_y, y_host, ybytes, cudaMemcpyHostToDevice, s));
+    EXACT_TRY(cudaMemcpyAsync(P.stage_x, x_host, xbytes, cudaMemcpyHostToDevice, s));
+    st = exact_solve(plan, P.stage_y, y_dtype, I0, eta, iters, opts, P.stage_x, info, stream);
+    if (st != EXACT_OK) {
+        cudaStreamSynchronize(s);
+        return st;
+    }
+    EXACT_TRY(cudaMemcpyAsync(x_host, P.stage_x, xbytes, cudaMemcpyDeviceToHost, s));
+    EXACT_TRY(cudaStreamSynchronize(s));
     return EXACT_OK;
 }
 
@@ -1438,7 +1682,8 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
         if (isnan(o.lo) || isnan(o.hi) || o.lo > o.hi || o.lo == INFINITY || o.hi == -INFINITY)
             return EXACT_ERR_INVALID_ARG;
         if (!isfin(o.tol) || o.tol < 0.0 || o.check_every < 0) return EXACT_ERR_INVALID_ARG;
-        if (o.average_tail || o.stop_rule != EXACT_STOP_RESIDUAL || o.tv_bound != 0.0 || o.prox_lambda != 0.0)
+        if (o.average_tail || o.stop_rule != EXACT_STOP_RESIDUAL || o.tv_bound != 0.0 || o.prox_lambda != 0.0 ||
+            o.t0 != 0 || o.total_iters != 0 || o.resume || o.x_last)
             return EXACT_ERR_UNSUPPORTED;
         for (int q = 0; q < j; ++q)
             if (jobs[q].plan == J.plan) return EXACT_ERR_INVALID_ARG;
@@ -1543,7 +1788,8 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
     for (int j = 0; j < n_jobs; ++j) {
         const exact_job &Jb = jobs[j];
         Plan &P = *reinterpret_cast<Plan *>(Jb.plan);
-        EXACT_TRY(launch_reset_state(P.state, s));
+        EXACT_TRY(launch_reset_state(P.state, 0, Jb.iters, Jb.opts.tol, Jb.opts.check_every, EXACT_STOP_RESIDUAL,
+                                     Jb.iters / 2, s));
         EXACT_TRY(reset_split_counts(P, s));
         EXACT_TRY(launch_collapse(Jb.y, Jb.y_dtype, P.W, P.n, P.Y, s));
         EXACT_TRY(launch_pack(Jb.x, P.xr[0], P.xc[0], P.g.nx, P.g.ny, P.ldr(), P.ldc(), (float)Jb.opts.lo,

@@ -100,11 +100,31 @@ struct DevState {
     double lam_prev;
     double inv_norm;  // power iteration: 1/||w|| for the next forward
     double avg_change;  // running-average rule: ||xbar_t - xbar_{t-1}||
+    // solve parameters, set at the start of a solve (k_reset_state): the
+    // iteration index one past this call's last, the stopping test and the
+    // first iteration index of the tail average (kernels launched from a
+    // CUDA graph loop read these instead of per-launch arguments)
+    int iter_end;
+    int check_every;
+    int rule;        // exact_stop_rule
+    int avg_from;
+    double tol;
 };
 
 // FP64 partial sums per adjoint tile of the full step: ||x_out - x_base||^2,
 // ||x_base||^2 and ||xbar_t - xbar_{t-1}||^2 (running-average rule).
 constexpr int kPartStride = 3;
+
+// One instantiated solve graph (a WHILE node over the iteration's kernels),
+// kept by the plan for relaunch while its key -- the kernel arguments that do
+// not come from the device state -- stays the same.
+struct SolveGraph {
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t last = nullptr;  // recorded after its latest launch
+    std::vector<unsigned char> key;
+    unsigned long long stamp = 0;  // last use (least recently used is replaced first)
+};
+constexpr int kSolveGraphs = 4;
 
 struct Plan {
     exact_geometry g;
@@ -136,6 +156,8 @@ struct Plan {
     float *split_part = nullptr;         // adjoint view split: partial tiles [tiles][kMaxSplit][kTH * kTW]
     int *split_count = nullptr;          // [tiles] arrival counts (zeroed when the workspace is bound)
     int adj_split = 1;                   // CTAs per adjoint tile (exact_plan_autotune / set_tuning)
+    float *stage_y = nullptr;            // exact_solve_host: device copy of the host counts [W][n]
+    float *stage_x = nullptr;            // exact_solve_host: device copy of the host image [d]
     double *xrd = nullptr, *xcd = nullptr;  // FP64 padded copies (power iteration)
     double *zd = nullptr;                // FP64 projections [n]
     float *w32 = nullptr;                // FP32 power-iteration image [d]
@@ -152,6 +174,9 @@ struct Plan {
     const float *bg_p = nullptr;     // caller-owned [bg_M][n]
     float bg_mu2[kMaxBg][kMaxK];     // mu_bg log2(e)
     std::vector<void *> captured_infos;  // solve-info payloads owned by captured graphs
+    cudaStream_t cap_stream = nullptr;   // stream the solve graphs' loop bodies are captured on
+    std::vector<SolveGraph> graphs;      // up to kSolveGraphs instantiated solve graphs
+    unsigned long long graph_clock = 0;
     // kernel timing (profiling aid): event pairs recorded around sampled launches
     int prof_every = 0;
     int prof_used = 0;              // event pairs recorded since the last read
@@ -235,6 +260,11 @@ struct AdjArgs {
     float *split_part;
     int *split_count;
     const DevState *state;
+    // iter_from_state != 0 (launches inside a CUDA graph loop): the iteration
+    // index is state->iters_done, avg_from is state->avg_from, and the
+    // running-average slots follow from them and hist_cap (the ring length)
+    int iter_from_state;
+    int hist_cap;
 };
 
 constexpr int kMaxSplit = 8;  // view split of the adjoint (autotuned per plan)
@@ -259,6 +289,12 @@ struct BatchJob {
 
 constexpr int kBatchThreads = 128;  // = kFR, and 4 adjoint warps
 constexpr int kMaxBatch = 256;      // jobs per batch launch
+
+// ---- host helpers shared by the plan code (api.cu) and exact_operator_static --
+// 2D tensor map of one padded image copy (box kFHB x kFC, zero fill outside).
+bool encode_map(CUtensorMap *map, float *base, long long ld, long long lines);
+// Link coefficients of a plan at source intensity I0.
+LinkCoef make_coef(const Plan &P, double I0);
 
 // ---- launchers (each returns cudaGetLastError()) ------------------------------
 cudaError_t launch_forward(const FwdArgs &a, bool link, const LinkCoef *coef, const CUtensorMap &map_r,
@@ -309,9 +345,17 @@ int tv_grid(long long d);
 TvTail *tv_tail(void *ws, int nx, int ny, int grid);
 cudaError_t launch_tv_project(const TvLaunch &L, cudaStream_t s);
 
-cudaError_t launch_solve_reduce(const double *partials, int nparts, DevState *st, int iter, double tol,
-                                int check_every, int rule, cudaStream_t s);
-cudaError_t launch_reset_state(DevState *st, cudaStream_t s);
+// FP64 stopping reduction of iteration `iter` (the stopping test comes from
+// the state).  The _cond form runs inside a CUDA graph's WHILE loop: the
+// iteration is state->iters_done and it sets the loop condition `cond` to
+// "not stopped and state->iters_done < state->iter_end".
+cudaError_t launch_solve_reduce(const double *partials, int nparts, DevState *st, int iter, cudaStream_t s);
+cudaError_t launch_solve_reduce_cond(const double *partials, int nparts, DevState *st,
+                                     cudaGraphConditionalHandle cond, cudaStream_t s);
+// Start of a solve call: iterations t0 .. t_end - 1 (0-based), stopping test
+// (tol, check_every, rule), tail average from iteration avg_from.
+cudaError_t launch_reset_state(DevState *st, int t0, int t_end, double tol, int check_every, int rule, int avg_from,
+                               cudaStream_t s);
 
 // FP64 power iteration pieces
 cudaError_t launch_power_init(double *xrd, double *xcd, int nx, int ny, long long ldr, long long ldc,

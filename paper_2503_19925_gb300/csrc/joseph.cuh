@@ -369,6 +369,24 @@ __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, l
         __syncthreads();
     }
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    // iteration index and running-average slots of this launch (from the
+    // device state inside a CUDA graph loop, the same values the host passes
+    // otherwise)
+    int it_idx = a.iter, avg_from = a.avg_from, hist_put = a.hist_put, hist_drop = a.hist_drop;
+    double inv_m = a.inv_m, inv_m_prev = a.inv_m_prev;
+    if (MODE == ADJ_EG_FINAL && a.iter_from_state) {
+        it_idx = a.state->iters_done;
+        avg_from = a.state->avg_from;
+        if (a.hist) {
+            // iterate number it enters the window of the last m = max(1, floor(it/2));
+            // when m did not grow, x_{it-m} leaves it
+            const int it = it_idx + 1, m = max(1, it / 2), mp = max(1, (it - 1) / 2);
+            hist_put = it % a.hist_cap;
+            hist_drop = (it >= 2 && m == mp) ? (it - m) % a.hist_cap : -1;
+            inv_m = 1.0 / (double)m;
+            inv_m_prev = it >= 2 ? 1.0 / (double)mp : 0.0;
+        }
+    }
     for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
         const int px = t % kTW, py = t / kTW;
         const float gsum = sm.stage[py][px];
@@ -396,12 +414,12 @@ __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, l
                     const long long dpix = (long long)a.nx * a.ny;
                     const double sp = a.avg[q];
                     double sn = sp + (double)xn;
-                    if (a.hist_drop >= 0) sn -= (double)a.hist[(long long)a.hist_drop * dpix + q];
-                    a.hist[(long long)a.hist_put * dpix + q] = xn;
+                    if (hist_drop >= 0) sn -= (double)a.hist[(long long)hist_drop * dpix + q];
+                    a.hist[(long long)hist_put * dpix + q] = xn;
                     a.avg[q] = sn;
-                    const double dv = sn * a.inv_m - sp * a.inv_m_prev;
+                    const double dv = sn * inv_m - sp * inv_m_prev;
                     s2 += dv * dv;
-                } else if (a.avg && a.iter >= a.avg_from) {
+                } else if (a.avg && it_idx >= avg_from) {
                     a.avg[q] += (double)xn;
                 }
                 const double dd = (double)xn - (double)xb;

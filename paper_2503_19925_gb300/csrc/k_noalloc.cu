@@ -15,14 +15,19 @@
 // stand-in, not a device address), so the first call on each device, with that
 // device current, asks the runtime for the array's device address
 // (cudaGetSymbolAddress) and keeps it; that first call should therefore come
-// before any stream capture.  All calls share the array and it keeps the last
-// call's contents: every scratch word a call reads is first written by the same
-// call (the padded copies are written whole, pads and alignment tails
-// included), so nothing needs clearing, but calls that overlap on the GPU
-// (different streams, or different plans at once) race on it.
+// before any stream capture.  The kept address belongs to the device's primary
+// context: after cudaDeviceReset (or any other teardown of that context) it is
+// stale, so the entry point must not be used again in that process.
+//
+// All calls share the array and it keeps the last call's contents: every
+// scratch word a call reads is first written by the same call (the padded
+// copies are written whole, pads and alignment tails included), so nothing
+// needs clearing, but calls that overlap on the GPU (different streams, or
+// different plans at once) race on it.  The adjoint runs one CTA per tile
+// (the plan's adj_split is not used: its partial tiles live in the workspace),
+// so F equals exact_operator's up to the FP32 summation order of a split.
 #include "joseph.cuh"
 
-#include <cudaTypedefs.h>
 #include <mutex>
 #include <string.h>
 
@@ -55,29 +60,6 @@ cudaError_t scratch_address(void **out)
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
-}
-
-// 2D tensor map (x = padded cross index, y = driving line) of one padded copy
-// in the static scratch; host-side encoding only, no device memory.
-bool encode_static_map(CUtensorMap *map, float *base, long long ld, long long lines)
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        cudaDriverEntryPointQueryResult q;
-        void *ptr = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !ptr)
-            return false;
-        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-    }
-    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)lines};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)kFHB, (cuuint32_t)kFC};
-    const cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 exact_status status_of(cudaError_t e)
@@ -119,17 +101,11 @@ exact_status exact_operator_static(exact_plan_t plan, const float *x, const void
     float *Y = reinterpret_cast<float *>(sp + b_xr + b_xc);
     float *r = reinterpret_cast<float *>(sp + b_xr + b_xc + b_n);
     CUtensorMap map_r, map_c;
-    if (!encode_static_map(&map_r, xr, P.ldr(), P.g.ny) || !encode_static_map(&map_c, xc, P.ldc(), P.g.nx))
+    if (!encode_map(&map_r, xr, P.ldr(), P.g.ny) || !encode_map(&map_c, xc, P.ldc(), P.g.nx))
         return EXACT_ERR_CUDA;
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    LinkCoef coef;
-    memset(&coef, 0, sizeof(coef));
-    for (int k = 0; k < P.K; ++k) {
-        coef.mu2[k] = P.mu_log2e[k];
-        coef.c[k] = (float)(I0 * (double)P.C[k]);
-        for (int m = 0; m < P.bg_M; ++m) coef.mub[m][k] = P.bg_mu2[m][k];
-    }
+    const LinkCoef coef = make_coef(P, I0);
     if ((e = launch_collapse(y, y_dtype, P.W, P.n, Y, s)) != cudaSuccess) return status_of(e);
     if ((e = launch_pack(x, xr, xc, P.g.nx, P.g.ny, P.ldr(), P.ldc(), 0.f, 0.f, false, s)) != cudaSuccess)
         return status_of(e);
@@ -166,6 +142,8 @@ exact_status exact_operator_static(exact_plan_t plan, const float *x, const void
     a.r = r;
     a.scale = (float)(1.0 / ((double)P.W * (double)P.n));
     a.out = F;
+    // nsplit stays 0: one CTA per adjoint tile whatever the plan's adj_split,
+    // as the split's partial tiles and arrival counts live in the workspace
     if ((e = launch_adjoint(a, ADJ_PLAIN, P.g.beam == 1, s)) != cudaSuccess) return status_of(e);
     return EXACT_OK;
 }

@@ -114,16 +114,27 @@ __device__ double block_sum_fixed(const double *src, int count, int stride)
     return r;
 }
 
+// COND: launched inside a CUDA graph's WHILE loop; the iteration index is
+// st->iters_done and thread 0 sets the loop condition on every launch (also
+// when the solve already stopped), so the loop always ends: iters_done grows by
+// one per iteration up to st->iter_end.
+template <bool COND>
 __global__ void __launch_bounds__(RT) k_solve_reduce(const double *partials, int nparts, DevState *st, int iter,
-                                                     double tol, int check_every, int rule)
+                                                     cudaGraphConditionalHandle cond)
 {
-    if (st->done) return;
+    if (st->done) {
+        if (COND && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+        return;
+    }
+    const int rule = st->rule;
     const double num = block_sum_fixed(partials, nparts, kPartStride);
     const double den = block_sum_fixed(partials + 1, nparts, kPartStride);
     const double chg = rule == EXACT_STOP_AVERAGE ? block_sum_fixed(partials + 2, nparts, kPartStride) : 0.0;
     if (threadIdx.x == 0) {
         const double rel = sqrt(num) / fmax(sqrt(den), 1e-30);
-        const int t = iter + 1;  // iterations run
+        const int t = (COND ? st->iters_done : iter) + 1;  // iterations run
+        const double tol = st->tol;
+        const int check_every = st->check_every;
         st->rel_res = rel;
         st->avg_change = (rule == EXACT_STOP_AVERAGE && t >= 2) ? sqrt(chg) : 0.0;
         st->iters_done = t;
@@ -135,19 +146,25 @@ __global__ void __launch_bounds__(RT) k_solve_reduce(const double *partials, int
         } else if (may_stop && tol > 0.0 && check_every > 0 && t % check_every == 0 && crit <= tol) {
             st->done = 1;
         }
+        if (COND) cudaGraphSetConditional(cond, (!st->done && t < st->iter_end) ? 1u : 0u);
     }
 }
 
-__global__ void k_reset_state(DevState *st)
+__global__ void k_reset_state(DevState *st, int t0, int t_end, double tol, int check_every, int rule, int avg_from)
 {
     st->done = 0;
-    st->iters_done = 0;
+    st->iters_done = t0;
     st->status = EXACT_OK;
     st->rel_res = 0.0;
     st->lam = 0.0;
     st->lam_prev = 0.0;
     st->inv_norm = 1.0;
     st->avg_change = 0.0;
+    st->iter_end = t_end;
+    st->check_every = check_every;
+    st->rule = rule;
+    st->avg_from = avg_from;
+    st->tol = tol;
 }
 
 __global__ void k_power_init(double *xrd, double *xcd, int nx, int ny, long long ldr, long long ldc, DevState *st)
@@ -276,16 +293,23 @@ cudaError_t launch_collapse(const void *y, int dtype, int W, long long n, float 
     return cudaGetLastError();
 }
 
-cudaError_t launch_solve_reduce(const double *partials, int nparts, DevState *st, int iter, double tol,
-                                int check_every, int rule, cudaStream_t s)
+cudaError_t launch_solve_reduce(const double *partials, int nparts, DevState *st, int iter, cudaStream_t s)
 {
-    k_solve_reduce<<<1, RT, 0, s>>>(partials, nparts, st, iter, tol, check_every, rule);
+    k_solve_reduce<false><<<1, RT, 0, s>>>(partials, nparts, st, iter, cudaGraphConditionalHandle{});
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset_state(DevState *st, cudaStream_t s)
+cudaError_t launch_solve_reduce_cond(const double *partials, int nparts, DevState *st,
+                                     cudaGraphConditionalHandle cond, cudaStream_t s)
 {
-    k_reset_state<<<1, 1, 0, s>>>(st);
+    k_solve_reduce<true><<<1, RT, 0, s>>>(partials, nparts, st, -1, cond);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_state(DevState *st, int t0, int t_end, double tol, int check_every, int rule, int avg_from,
+                               cudaStream_t s)
+{
+    k_reset_state<<<1, 1, 0, s>>>(st, t0, t_end, tol, check_every, rule, avg_from);
     return cudaGetLastError();
 }
 

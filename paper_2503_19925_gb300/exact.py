@@ -64,7 +64,9 @@ class _SolveOpts(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_double), ("hi", ctypes.c_double), ("tol", ctypes.c_double),
                 ("check_every", ctypes.c_int), ("average_tail", ctypes.c_int), ("stop_rule", ctypes.c_int),
                 ("history_cap", ctypes.c_int), ("history", ctypes.c_void_p), ("tv_bound", ctypes.c_double),
-                ("tv", _TvOpts), ("prox_lambda", ctypes.c_double)]
+                ("tv", _TvOpts), ("prox_lambda", ctypes.c_double), ("t0", ctypes.c_int),
+                ("total_iters", ctypes.c_int), ("resume", ctypes.c_void_p), ("x_last", ctypes.c_void_p),
+                ("launch", ctypes.c_int), ("pad", ctypes.c_int)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -97,8 +99,11 @@ _SIGS = [
     ("exact_operator", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP, _VP]),
     ("exact_operator_static", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, _VP, _VP]),
     ("exact_solve_opts_default", _SolveOpts, []),
+    ("exact_solve_resume_bytes", ctypes.c_size_t, [_VP]),
     ("exact_solve", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    ctypes.POINTER(_SolveOpts), _VP, ctypes.POINTER(_SolveInfo), _VP]),
+    ("exact_solve_host", ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        ctypes.POINTER(_SolveOpts), _VP, ctypes.POINTER(_SolveInfo), _VP]),
     ("exact_norm_estimate", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int), _VP]),
     ("exact_norm_estimate_f32", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
@@ -130,6 +135,8 @@ _SIGS = [
                                             _VP]),
     ("exact_profile_enable", ctypes.c_int, [_VP, ctypes.c_int]),
     ("exact_profile_read", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    ("exact_probe_gather_ceiling", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                                  _VP]),
     ("exact_status_string", _CP, [ctypes.c_int]),
 ]
 
@@ -237,6 +244,16 @@ def tv_project(z: torch.Tensor, tau: float, lo: float = 0.0, hi: float = math.in
                                                     ctypes.byref(o), _ptr(x), _ptr(ws), nb, ctypes.byref(info),
                                                     _stream()))
     return x, TvInfo(info.rounds, info.solves, info.lam, info.status)
+
+
+def gather_ceiling() -> tuple[float, int]:
+    """Measured shared-memory gather rate of the current device (words/s) and
+    its SM count (exact_probe_gather_ceiling; synchronises)."""
+    w = ctypes.c_double()
+    n = ctypes.c_int()
+    _check("exact_probe_gather_ceiling", load().exact_probe_gather_ceiling(ctypes.byref(w), ctypes.byref(n),
+                                                                           _stream()))
+    return w.value, n.value
 
 
 class Dense:
@@ -404,32 +421,60 @@ class Plan:
                                                        _stream()))
         return F
 
+    def resume_state(self) -> torch.Tensor:
+        """A device buffer for the ``resume`` option of :meth:`solve`
+        (exact_solve_resume_bytes; FP64 averaging sums and the TV lam pair)."""
+        nb = int(load().exact_solve_resume_bytes(self._h))
+        return torch.zeros(nb // 8, dtype=torch.float64, device=self.device)
+
     def solve(self, y: torch.Tensor, I0: float, eta: float, iters: int, x: torch.Tensor | None = None,
               lo: float = 0.0, hi: float = math.inf, tol: float = 0.0, check_every: int = 1,
               average_tail: bool = False, stop_rule: str = "residual", tv_bound: float = 0.0,
-              tv_opts: dict | None = None, prox_lambda: float = 0.0, sync: bool = True):
+              tv_opts: dict | None = None, prox_lambda: float = 0.0, sync: bool = True, t0: int = 0,
+              total_iters: int = 0, resume: torch.Tensor | None = None, x_last: torch.Tensor | None = None,
+              history: torch.Tensor | None = None, launch: str = "auto"):
         """Run up to ``iters`` extragradient iterations in place on ``x``
         (zeros if None).  stop_rule "residual" tests the relative change of the
         iterate, "average" the change of the running average of the last half
         of the iterates (and returns that average; its window ring is
-        allocated here).  tv_bound > 0 intersects the box with the TV ball of
-        that radius (tv_opts: fields of exact_tv_opts to change).  Returns
-        (x, SolveInfo); with sync=False the info is filled once the current
-        stream reaches the end of the solve."""
+        allocated here unless ``history`` is given).  tv_bound > 0 intersects
+        the box with the TV ball of that radius (tv_opts: fields of
+        exact_tv_opts to change).  t0 / total_iters / resume / x_last continue
+        an earlier call of the same solve (see exact_solve_opts); launch
+        "auto" loops on the device in a CUDA graph where possible, "stream"
+        launches every kernel from the host.  Returns (x, SolveInfo); with
+        sync=False the info is filled once the current stream reaches the end
+        of the solve."""
         dt = self._y(y)
         if x is None:
             x = torch.zeros(self.shape_img, dtype=torch.float32, device=self.device)
         self._t(x, self.shape_img, name="x")
         if stop_rule not in STOP_RULES:
             raise ValueError(f"stop_rule must be one of {sorted(STOP_RULES)}")
+        if launch not in ("auto", "stream"):
+            raise ValueError("launch must be 'auto' or 'stream'")
         hist = None
         if stop_rule == "average":
-            cap = max(1, int(iters) // 2)
-            hist = torch.empty((cap,) + tuple(self.shape_img), dtype=torch.float32, device=self.device)
+            if history is not None:
+                hist = history
+                if hist.dtype != torch.float32 or hist.device != self.device or not hist.is_contiguous() or \
+                        tuple(hist.shape[1:]) != tuple(self.shape_img):
+                    raise ValueError("history must be a contiguous float32 [cap][ny][nx] tensor on the plan's device")
+            else:
+                cap = max(1, (int(t0) + int(iters)) // 2)
+                hist = torch.empty((cap,) + tuple(self.shape_img), dtype=torch.float32, device=self.device)
+        if resume is not None and (resume.dtype != torch.float64 or resume.device != self.device
+                                   or not resume.is_contiguous()
+                                   or resume.numel() * 8 < load().exact_solve_resume_bytes(self._h)):
+            raise ValueError("resume must come from resume_state()")
+        if x_last is not None:
+            self._t(x_last, self.shape_img, name="x_last")
         opts = _SolveOpts(float(lo), float(hi), float(tol), int(check_every), int(bool(average_tail)),
                           STOP_RULES[stop_rule], 0 if hist is None else hist.shape[0],
                           None if hist is None else hist.data_ptr(), float(tv_bound), tv_options(tv_opts),
-                          float(prox_lambda))
+                          float(prox_lambda), int(t0), int(total_iters),
+                          None if resume is None else resume.data_ptr(),
+                          None if x_last is None else x_last.data_ptr(), 0 if launch == "auto" else 1, 0)
         info = _SolveInfo()
         _check("exact_solve", load().exact_solve(self._h, _ptr(y), dt, float(I0), float(eta), int(iters),
                                                  ctypes.byref(opts), _ptr(x), ctypes.byref(info), _stream()))
@@ -512,20 +557,25 @@ class Plan:
         return {n: (ms[i], cnt[i]) for i, n in enumerate(names)}
 
     def solve_host(self, y_host: torch.Tensor, I0: float, eta: float, iters: int, x_host: torch.Tensor,
-                   y_dev: torch.Tensor | None = None, x_dev: torch.Tensor | None = None, **opts):
-        """Solve from host buffers: copy y and x_1 from (pinned) host memory,
-        solve on the device, copy the result back into ``x_host``.  All copies
-        are enqueued on the current stream; returns (x_host, SolveInfo) after
-        synchronising."""
-        if y_dev is None:
-            y_dev = torch.empty(y_host.shape, dtype=y_host.dtype, device=self.device)
-        if x_dev is None:
-            x_dev = torch.empty(x_host.shape, dtype=x_host.dtype, device=self.device)
-        y_dev.copy_(y_host, non_blocking=True)
-        x_dev.copy_(x_host, non_blocking=True)
-        _, info = self.solve(y_dev, I0, eta, iters, x=x_dev, sync=False, **opts)
-        x_host.copy_(x_dev, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+                   lo: float = 0.0, hi: float = math.inf, tol: float = 0.0, check_every: int = 1):
+        """Solve from host buffers (exact_solve_host): the library copies y and
+        x_1 from (pinned) host memory into the plan's workspace, solves, and
+        copies the result back into ``x_host``, on the current stream, and
+        synchronises.  Returns (x_host, SolveInfo)."""
+        for t, name in ((y_host, "y_host"), (x_host, "x_host")):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous host tensor")
+        if y_host.dtype not in (torch.float32, torch.bfloat16) or y_host.numel() != self.W * self.n_rays:
+            raise ValueError("y_host must hold [n_windows][n_views][n_bins] float32 or bfloat16 counts")
+        if x_host.dtype != torch.float32 or x_host.numel() != self.shape_img[0] * self.shape_img[1]:
+            raise ValueError("x_host must be a float32 [ny][nx] tensor")
+        dt = F32 if y_host.dtype == torch.float32 else BF16
+        opts = load().exact_solve_opts_default()
+        opts.lo, opts.hi, opts.tol, opts.check_every = float(lo), float(hi), float(tol), int(check_every)
+        info = _SolveInfo()
+        _check("exact_solve_host", load().exact_solve_host(self._h, _ptr(y_host), dt, float(I0), float(eta),
+                                                           int(iters), ctypes.byref(opts), _ptr(x_host),
+                                                           ctypes.byref(info), _stream()))
         return x_host, info
 
     def recommended_eta(self, I0: float, normA_sq: float) -> float:
@@ -587,7 +637,7 @@ class Batch:
             xs.append(x)
             arr[k] = _Job(p._h.value, jb.y.data_ptr(), dt, float(jb.I0), float(jb.eta), int(jb.iters),
                           _SolveOpts(float(jb.lo), float(jb.hi), float(jb.tol), int(jb.check_every), 0, 0, 0, None,
-                                     0.0, tv_options(None), 0.0),
+                                     0.0, tv_options(None), 0.0, 0, 0, None, None, 0, 0),
                           x.data_ptr(), ctypes.pointer(infos[k]))
         return arr, infos, xs
 

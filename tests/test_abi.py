@@ -46,7 +46,9 @@ def test_struct_layouts_match(tmp_path):
                    'printf("%zu %zu %zu %zu %zu\\n", sizeof(exact_solve_opts), offsetof(exact_solve_opts, average_tail),'
                    ' offsetof(exact_solve_opts, history), offsetof(exact_solve_opts, tv_bound),'
                    ' offsetof(exact_solve_opts, tv));\n'
-                   'printf("%zu\\n", offsetof(exact_solve_opts, prox_lambda));\n'
+                   'printf("%zu %zu %zu %zu %zu\\n", offsetof(exact_solve_opts, prox_lambda),'
+                   ' offsetof(exact_solve_opts, t0), offsetof(exact_solve_opts, resume),'
+                   ' offsetof(exact_solve_opts, x_last), offsetof(exact_solve_opts, launch));\n'
                    'printf("%zu %zu %zu\\n", sizeof(exact_solve_info), offsetof(exact_solve_info, status),'
                    ' offsetof(exact_solve_info, avg_change));\n'
                    'printf("%zu %zu\\n", sizeof(exact_spectrum), sizeof(exact_windows));\n'
@@ -65,7 +67,9 @@ def test_struct_layouts_match(tmp_path):
     o = [int(v) for v in out[1].split()]
     assert o == [ctypes.sizeof(b._SolveOpts), b._SolveOpts.average_tail.offset, b._SolveOpts.history.offset,
                  b._SolveOpts.tv_bound.offset, b._SolveOpts.tv.offset]
-    assert int(out[2]) == b._SolveOpts.prox_lambda.offset
+    assert [int(v) for v in out[2].split()] == [b._SolveOpts.prox_lambda.offset, b._SolveOpts.t0.offset,
+                                                 b._SolveOpts.resume.offset, b._SolveOpts.x_last.offset,
+                                                 b._SolveOpts.launch.offset]
     out = out[:2] + out[3:]
     i = [int(v) for v in out[2].split()]
     assert i == [ctypes.sizeof(b._SolveInfo), b._SolveInfo.status.offset, b._SolveInfo.avg_change.offset]

@@ -38,15 +38,22 @@ def requests():
     return out
 
 
-def test_served_equals_alone_and_plain(requests):
-    server = Server(budget_bytes=4e9, max_slots=8, round_iters=10)
-    mixed = {r.tag: r for r in server.run(requests, realtime=True)}
+@pytest.mark.parametrize("mode", ["streams", "rounds"])
+def test_served_equals_alone_and_plain(requests, mode):
+    """Streams mode: all requests resident at once, their solves overlapping
+    on the device, each bitwise its plain solve.  Rounds mode: arrivals join
+    running rounds, results within 1e-4 of the plain solve."""
+    server = Server(budget_bytes=4e9, max_slots=8, round_iters=10, mode=mode)
+    mixed = {r.tag: r for r in server.run(requests, realtime=mode == "rounds")}
     server.close()
     assert sorted(mixed) == list(range(len(requests)))
-    assert server.rounds > 1
+    if mode == "rounds":
+        assert server.rounds > 1
+    else:
+        assert server.peak_resident >= 2  # solves overlapped on the device
     plain = {r.tag: r for r in serve_sequential(requests, realtime=False)}
     for req in requests:
-        alone_server = Server(budget_bytes=4e9, max_slots=8, round_iters=10)
+        alone_server = Server(budget_bytes=4e9, max_slots=8, round_iters=10, mode=mode)
         alone = alone_server.run([req], realtime=False)[0]
         alone_server.close()
         m = mixed[req.tag]
@@ -55,6 +62,8 @@ def test_served_equals_alone_and_plain(requests):
         assert rel_l2(m.x.double().numpy(), plain[req.tag].x.double().numpy()) <= 1e-4
         assert abs(m.iters - plain[req.tag].iters) <= 1
         assert m.rel_res <= req.tol or m.iters == req.max_iters
+        if mode == "streams":
+            assert torch.equal(m.x, plain[req.tag].x) and m.iters == plain[req.tag].iters
 
 
 def test_budget_limits_residency(requests):
