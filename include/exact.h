@@ -497,6 +497,29 @@ exact_status exact_profile_read(exact_plan_t plan, double ms[EXACT_PROF_KINDS],
  * sm_count (may be NULL) receives the device's SM count.  Synchronises. */
 exact_status exact_probe_gather_ceiling(double *words_per_s, int *sm_count, exact_stream_t stream);
 
+/* Fault injection for tests of the bounded device waits (no counterpart in the
+ * paper).  Every device-side wait of this library -- the forward's staging
+ * copies, the persistent batch kernel's waits for the previous phase of a job,
+ * the TV projection's grid barriers -- gives up after a bounded number of polls
+ * and reports EXACT_ERR_TIMEOUT instead of hanging; every thread block then
+ * leaves and the device stays usable.  These switches let a test make such a
+ * wait run out on purpose:
+ *  - EXACT_INJECT_WAIT_POLLS, value >= 0: polls before a batch dependency wait
+ *    or a TV grid barrier gives up (0: the built-in limits, seconds each);
+ *  - EXACT_INJECT_BLOCK_BATCH_JOB, value = job index (-1: none): in the next
+ *    exact_batch_solve that job's later phases wait for more completions than
+ *    the job has items, so its wait runs out (EXACT_ERR_TIMEOUT in its info)
+ *    and the launch ends;
+ *  - EXACT_INJECT_BLOCK_TV_BARRIER, value != 0: the next TV projection launch
+ *    (exact_tv_project, exact_tv_prox, or a solve with tv_bound / prox_lambda)
+ *    starts its grid barrier's arrival count at the grid size, so the barrier
+ *    never completes and the call reports EXACT_ERR_TIMEOUT.
+ * The blocks are one-shot; the settings are process-wide. */
+#define EXACT_INJECT_WAIT_POLLS 1
+#define EXACT_INJECT_BLOCK_BATCH_JOB 2
+#define EXACT_INJECT_BLOCK_TV_BARRIER 3
+exact_status exact_debug_inject(int kind, long long value);
+
 /* Static description of a status code. */
 const char *exact_status_string(exact_status status);
 

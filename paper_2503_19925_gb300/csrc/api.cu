@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <map>
+#include <atomic>
 #include <mutex>
 
 #include <climits>
@@ -612,6 +613,17 @@ bool encode_map(CUtensorMap *map, float *base, long long ld, long long lines)
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// ---- fault injection (exact_debug_inject) ----
+namespace {
+std::atomic<long long> g_wait_polls{0};
+std::atomic<int> g_block_batch_job{-1};
+std::atomic<int> g_block_tv{0};
+}  // namespace
+
+long long debug_wait_polls() { return g_wait_polls.load(); }
+int debug_take_batch_block() { return g_block_batch_job.exchange(-1); }
+bool debug_take_tv_block() { return g_block_tv.exchange(0) != 0; }
+
 LinkCoef make_coef(const Plan &P, double I0)
 {
     LinkCoef c;
@@ -641,6 +653,24 @@ const char *exact_status_string(exact_status s)
     case EXACT_ERR_NO_WORKSPACE: return "no workspace bound";
     }
     return "unknown status";
+}
+
+exact_status exact_debug_inject(int kind, long long value)
+{
+    switch (kind) {
+    case EXACT_INJECT_WAIT_POLLS:
+        if (value < 0) return EXACT_ERR_INVALID_ARG;
+        g_wait_polls.store(value);
+        return EXACT_OK;
+    case EXACT_INJECT_BLOCK_BATCH_JOB:
+        if (value < -1 || value >= kMaxBatch) return EXACT_ERR_INVALID_ARG;
+        g_block_batch_job.store((int)value);
+        return EXACT_OK;
+    case EXACT_INJECT_BLOCK_TV_BARRIER:
+        g_block_tv.store(value != 0 ? 1 : 0);
+        return EXACT_OK;
+    }
+    return EXACT_ERR_INVALID_ARG;
 }
 
 exact_solve_opts exact_solve_opts_default(void)
@@ -1778,6 +1808,8 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
     for (int j = 0; j < n_jobs; ++j)
         if ((unsigned long long)hj[j].phase_off[5] * (unsigned long long)(rounds + 1) >= (1ULL << 32))
             return EXACT_ERR_UNSUPPORTED;
+    const int held = debug_take_batch_block();
+    if (held >= 0 && held < n_jobs) hj[held].hold = (unsigned)hj[held].phase_off[5] * (unsigned)rounds + 1u;
 
     EXACT_TRY(cudaMemcpyAsync(B->dev, B->host, B->L.total, cudaMemcpyHostToDevice, s));
     if (cap == cudaStreamCaptureStatusNone) {
@@ -1799,7 +1831,7 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
     }
     EXACT_TRY(launch_batch(reinterpret_cast<const BatchJob *>(B->dev + B->L.jobs), n_jobs,
                            reinterpret_cast<const int *>(B->dev + B->L.prefix), rounds, B->next, B->done_items,
-                           B->abort_flag, B->grid, s));
+                           B->abort_flag, B->grid, debug_wait_polls(), s));
     for (int j = 0; j < n_jobs; ++j) {
         const exact_job &Jb = jobs[j];
         Plan &P = *reinterpret_cast<Plan *>(Jb.plan);

@@ -285,7 +285,16 @@ struct BatchJob {
     int iters, check_every;
     double tol;
     int phase_off[6];          // items of the job before phase p within a round; [5] = items per round
+    unsigned hold;             // fault injection: nonzero, phases >= 1 wait for this many completions
+                               // (more than the job has items, so the wait runs out); 0: normal
 };
+
+// Fault injection for tests of the bounded device waits (exact_debug_inject):
+// the poll limit of the batch dependency waits and the TV grid barriers (0:
+// the built-in limits), and one-shot blocks of the next batch job / TV launch.
+long long debug_wait_polls();
+int debug_take_batch_block();  // job index to block in the next batch launch, or -1
+bool debug_take_tv_block();    // block the next TV launch's grid barrier
 
 constexpr int kBatchThreads = 128;  // = kFR, and 4 adjoint warps
 constexpr int kMaxBatch = 256;      // jobs per batch launch
@@ -372,7 +381,7 @@ cudaError_t launch_adjoint_d(const RayD *rays, const ViewRec *views, int n_views
 // (phase-major), rounds = largest iteration count.  next/done_items/abort are
 // zeroed by the caller.
 cudaError_t launch_batch(const BatchJob *jobs, int n_jobs, const int *prefix, int rounds, unsigned long long *next,
-                         unsigned *done_items, int *abort_flag, int grid, cudaStream_t s);
+                         unsigned *done_items, int *abort_flag, int grid, long long dep_polls, cudaStream_t s);
 int batch_grid_size();
 
 cudaError_t launch_power_reduce(const double *pz, int nz, const double *pw, int nw, DevState *st, int iter,

@@ -95,7 +95,7 @@ __device__ void batch_reduce(const BatchJob &J, int iter, double *scratch)
 __global__ void __launch_bounds__(kBatchThreads, 6) k_batch(const BatchJob *__restrict__ jobs, int n_jobs,
                                                          const int *__restrict__ prefix_g, int rounds,
                                                          unsigned long long *next, unsigned *done_items,
-                                                         int *abort_flag)
+                                                         int *abort_flag, long long dep_polls)
 {
     __shared__ BatchSmem sm;
     const int t = threadIdx.x;
@@ -128,18 +128,21 @@ __global__ void __launch_bounds__(kBatchThreads, 6) k_batch(const BatchJob *__re
         const BatchJob &J = jobs[j];
 
         if (t == 0) {
-            const unsigned need = (unsigned)round * (unsigned)J.phase_off[5] + (unsigned)J.phase_off[phase];
+            // (a held job's later phases wait for more completions than it has items)
+            const unsigned need = (phase >= 1 && J.hold)
+                                      ? J.hold
+                                      : (unsigned)round * (unsigned)J.phase_off[5] + (unsigned)J.phase_off[phase];
             int ok = ld_volatile(abort_flag) ? 0 : 1;
             long long spins = 0;
             while (ok && ld_acquire(done_items + j) < need) {
-                if (ld_volatile(abort_flag) || ++spins > kDepSpins) {
+                if (ld_volatile(abort_flag) || ++spins > dep_polls) {
                     ok = 0;
                     break;
                 }
                 __nanosleep(64);
             }
             if (!ok) {
-                if (!ld_volatile(abort_flag) && spins > kDepSpins) {
+                if (!ld_volatile(abort_flag) && spins > dep_polls) {
                     J.state->status = EXACT_ERR_TIMEOUT;
                     J.state->done = 1;
                     atomicExch(abort_flag, 1);
@@ -211,10 +214,11 @@ int batch_grid_size()
 }
 
 cudaError_t launch_batch(const BatchJob *jobs, int n_jobs, const int *prefix, int rounds, unsigned long long *next,
-                         unsigned *done_items, int *abort_flag, int grid, cudaStream_t s)
+                         unsigned *done_items, int *abort_flag, int grid, long long dep_polls, cudaStream_t s)
 {
     if (n_jobs <= 0 || rounds <= 0) return cudaSuccess;
-    k_batch<<<grid, kBatchThreads, 0, s>>>(jobs, n_jobs, prefix, rounds, next, done_items, abort_flag);
+    k_batch<<<grid, kBatchThreads, 0, s>>>(jobs, n_jobs, prefix, rounds, next, done_items, abort_flag,
+                                           dep_polls > 0 ? dep_polls : kDepSpins);
     return cudaGetLastError();
 }
 

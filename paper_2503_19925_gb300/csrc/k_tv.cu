@@ -51,6 +51,7 @@ struct TvArgs {
     float *dual[8];        // px, py, rx, ry and their second buffers
     double *part;          // [2][grid] FP64 partial sums
     unsigned *bar;         // [0] arrivals, [1] generation
+    long long bar_polls;   // polls before a barrier wait gives up
     int *err;              // status word (EXACT_ERR_TIMEOUT on a barrier timeout)
     int *done;             // solve path: set with err on a timeout, and checked on entry
     double *lam_io;        // in: starting lam (<= 0: 1); out: last lam
@@ -75,7 +76,7 @@ __device__ __forceinline__ int ld_volatile_i32(const int *p)
 
 // Grid-wide barrier with a bounded wait.  Returns false (uniformly within the
 // CTA) if it gave up; the status word then holds EXACT_ERR_TIMEOUT.
-__device__ bool grid_barrier(unsigned *bar, int *err, int *done)
+__device__ bool grid_barrier(unsigned *bar, int *err, int *done, long long polls)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -90,7 +91,7 @@ __device__ bool grid_barrier(unsigned *bar, int *err, int *done)
         } else {
             long long spins = 0;
             while (ld_acquire_u32(bar + 1) == gen) {
-                if (++spins > kTvBarrierSpins || ld_volatile_i32(err) != 0) {
+                if (++spins > polls || ld_volatile_i32(err) != 0) {
                     ok = 0;
                     atomicCAS(err, 0, (int)EXACT_ERR_TIMEOUT);
                     break;
@@ -133,7 +134,7 @@ __device__ double grid_sum(const TvArgs &a, double v, int slot, bool &ok)
 {
     const double b = block_sum(v);
     if (threadIdx.x == 0) a.part[(long long)slot * gridDim.x + blockIdx.x] = b;
-    ok = grid_barrier(a.bar, a.err, a.done);
+    ok = grid_barrier(a.bar, a.err, a.done, a.bar_polls);
     double s = 0.0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += kTvThreads)
         s += __ldcg(a.part + (long long)slot * gridDim.x + i);
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(kTvThreads, 2) k_tv_project(TvArgs a)
     int rounds = 0, solves = 0;
     for (int k = 1; k <= a.max_dyk; ++k) {
         for (long long q = first; q < a.d; q += stride) a.w[q] = __ldcg(a.zk + q) + __ldcg(a.pk + q);
-        if (!grid_barrier(a.bar, a.err, a.done)) return;
+        if (!grid_barrier(a.bar, a.err, a.done, a.bar_polls)) return;
         double part = 0.0;
         double tw = 0.0;
         if (!a.fixed_lam) {
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(kTvThreads, 2) k_tv_project(TvArgs a)
                     // the first block starts r at p, the carried dual
                     fgp_block(a, sm, it == 0 ? px : rx, it == 0 ? py : ry, px, py, px2, py2, rx2, ry2, theta, step,
                               t, ns);
-                    if (!grid_barrier(a.bar, a.err, a.done)) return;
+                    if (!grid_barrier(a.bar, a.err, a.done, a.bar_polls)) return;
                     float *tp;
                     tp = px; px = px2; px2 = tp;
                     tp = py; py = py2; py2 = tp;
@@ -536,8 +537,17 @@ cudaError_t launch_tv_project(const TvLaunch &L, cudaStream_t s)
     a.hi = L.fixed_lam ? INFINITY : L.hi;
     a.fixed_lam = L.fixed_lam;
     if (L.fixed_lam) a.max_dyk = 1;
+    a.bar_polls = debug_wait_polls() > 0 ? debug_wait_polls() : kTvBarrierSpins;
     cudaError_t e = cudaMemsetAsync(tail->bar, 0, sizeof(tail->bar), s);
     if (e != cudaSuccess) return e;
+    if (debug_take_tv_block()) {
+        // fault injection: arrivals start at the grid size, so no arrival
+        // completes the first barrier and every CTA's wait runs out
+        const unsigned g = (unsigned)L.grid;
+        e = cudaMemcpyAsync(tail->bar, &g, sizeof(g), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // g lives on this stack frame
+        if (e != cudaSuccess) return e;
+    }
     void *args[] = {&a};
     return cudaLaunchCooperativeKernel((const void *)k_tv_project, dim3(L.grid), dim3(kTvThreads), args,
                                        sizeof(TvSmem), s);

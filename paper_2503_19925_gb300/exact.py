@@ -137,6 +137,7 @@ _SIGS = [
     ("exact_profile_read", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     ("exact_probe_gather_ceiling", ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                                   _VP]),
+    ("exact_debug_inject", ctypes.c_int, [ctypes.c_int, ctypes.c_longlong]),
     ("exact_status_string", _CP, [ctypes.c_int]),
 ]
 
