@@ -215,11 +215,14 @@ exact_status exact_dense_solve(exact_dense_t dense, const double *y, double I0, 
                                double hi, double *x, const double *x_true, double *err, exact_stream_t stream);
 
 /* Kernel tuning of a plan (no counterpart in the paper: a property of this
- * implementation).  adj_split: CTAs sharing one 16 x 16-pixel tile of the
- * adjoint, each taking an interleaved subset of the views (1..8); the tile's
- * partial sums are added in split order, so results are deterministic for a
- * given value and differ only in FP32 rounding between values.  Small images
- * want larger splits (more CTAs than tiles).  reserved must be zero. */
+ * implementation).  adj_split: CTAs sharing one 32 x 32-pixel tile of the
+ * adjoint, each taking an interleaved subset of the views (1..16, and at most
+ * the plan's limit: about 64 CTAs per SM in all, else EXACT_ERR_UNSUPPORTED;
+ * the workspace holds one partial tile per split); the tile's partial sums
+ * are added in split order, so results are deterministic for a given value
+ * and differ only in FP32 rounding between values.  A new plan starts with
+ * the largest of {1, 2, 3, 4, 6, 8, 12, 16} that keeps about 14 CTAs per SM.
+ * reserved must be zero. */
 typedef struct {
     int adj_split;
     int reserved[7];
@@ -229,7 +232,7 @@ exact_status exact_plan_get_tuning(exact_plan_t plan, exact_tuning *out);
 exact_status exact_plan_set_tuning(exact_plan_t plan, const exact_tuning *tuning);
 
 /* Autotuner: times the adjoint of this plan's geometry on the device for
- * adj_split in {1, 2, 3, 4, 6, 8} (9 rounds after a warm-up round, one launch
+ * adj_split in {1, 2, 3, 4, 6, 8, 12, 16} within the plan's limit (9 rounds after a warm-up round, one launch
  * of each value per round; median per value) and keeps the fastest, a larger
  * split only when it is more than 1% faster.  The choice is
  * cached per geometry shape (beam, nx, ny, n_views, n_bins) for the life of

@@ -360,7 +360,7 @@ size_t carve(Plan &P, char *base)
     P.zd = c.take<double>(base, (size_t)P.n);
     P.w32 = c.take<float>(base, (size_t)P.d);
     P.state = c.take<DevState>(base, 1);
-    P.split_part = c.take<float>(base, (size_t)nb_adj * kMaxSplit * kTH * kTW);
+    P.split_part = c.take<float>(base, (size_t)nb_adj * P.max_split * kTH * kTW);
     P.split_count = c.take<int>(base, (size_t)nb_adj);
     P.tv_step = c.take<float>(base, (size_t)P.d);
     P.tv_lam = c.take<double>(base, 2);
@@ -436,19 +436,37 @@ void prof_end(Plan &P, int u, cudaStream_t s)
     if (u >= 0) cudaEventRecord(P.prof_ev[2 * u + 1], s);
 }
 
-// View split of a new plan's adjoint, before any autotuning: the largest of
-// {1, 2, 3, 4, 6, 8} that keeps tiles x split within about 27 CTAs per SM
-// (four waves of the 7 adjoint CTAs resident per SM).  Small images get more
-// CTAs than they have tiles; the 512^2 images of the headline workload get 4,
-// which is what the autotuner measures best there.
-int default_split(const Plan &P)
+constexpr int kSplitCandidates[] = {1, 2, 3, 4, 6, 8, 12, 16};
+
+int device_sms(int device)
 {
     int sms = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P.device) != cudaSuccess || sms <= 0) sms = 1;
-    const long long tiles = adjoint_blocks(P.g.nx, P.g.ny), want = 27LL * sms;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) sms = 1;
+    return sms;
+}
+
+// Largest view split a plan supports (its workspace holds that many partial
+// tiles per tile): up to kMaxSplit while tiles x split stays within about 64
+// CTAs per SM; more only adds partial tiles to combine.
+int max_split(const Plan &P)
+{
+    const long long tiles = adjoint_blocks(P.g.nx, P.g.ny), cap = 64LL * device_sms(P.device);
     int best = 1;
-    for (int s : {1, 2, 3, 4, 6, 8})
-        if (tiles * s <= want) best = s;
+    for (int s : kSplitCandidates)
+        if (s <= kMaxSplit && tiles * s <= cap) best = s;
+    return best;
+}
+
+// View split of a new plan's adjoint, before any autotuning: the largest
+// candidate that keeps tiles x split within about 14 CTAs per SM (two waves
+// of the 7 adjoint CTAs resident per SM; larger splits measured no faster at
+// 512^2).  Small images get more CTAs than they have tiles.
+int default_split(const Plan &P)
+{
+    const long long tiles = adjoint_blocks(P.g.nx, P.g.ny), want = 14LL * device_sms(P.device);
+    int best = 1;
+    for (int s : kSplitCandidates)
+        if (s <= P.max_split && tiles * s <= want) best = s;
     return best;
 }
 
@@ -820,6 +838,18 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
     if (e == cudaSuccess) e = cudaMalloc(&P->ray_delta, sizeof(float) * rdelta.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->rays_d, sizeof(RayD) * rd.size());
     if (e == cudaSuccess) e = cudaMalloc(&P->views, sizeof(ViewRec) * vw.size());
+    // the adjoint's per-axis view lists: views with x-driven rays, then views
+    // with y-driven rays (a fan crossing a diagonal is in both)
+    std::vector<int> vit;
+    for (int v = 0; v < g.n_views; ++v)
+        if (vw[v].xb1 > vw[v].xb0) vit.push_back(v);
+    P->nxv = (int)vit.size();
+    for (int v = 0; v < g.n_views; ++v)
+        if (vw[v].yb1 > vw[v].yb0) vit.push_back(v);
+    P->nyv = (int)vit.size() - P->nxv;
+    if (vit.empty()) vit.push_back(0);
+    if (e == cudaSuccess) e = cudaMalloc(&P->vitems, sizeof(int) * vit.size());
+    put(P->vitems, vit.data(), sizeof(int) * vit.size());
     put(P->rays_w, rw.data(), sizeof(RayW) * rw.size());
     put(P->units, units.data(), sizeof(FwdUnit) * units.size());
     put(P->kstart, kst.data(), sizeof(int) * kst.size());
@@ -838,6 +868,7 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
         exact_plan_destroy(reinterpret_cast<exact_plan_t>(P));
         return cuda_status(e);
     }
+    P->max_split = max_split(*P);
     P->adj_split = default_split(*P);
     memset(P->host_state, 0, sizeof(DevState));
     *out = reinterpret_cast<exact_plan_t>(P);
@@ -859,6 +890,7 @@ exact_status exact_plan_destroy(exact_plan_t plan)
     if (P->ray_delta) cudaFree(P->ray_delta);
     if (P->rays_d) cudaFree(P->rays_d);
     if (P->views) cudaFree(P->views);
+    if (P->vitems) cudaFree(P->vitems);
     free_solve_graphs(*P);
     if (P->host_state) cudaFreeHost(P->host_state);
     if (P->prof_ev) prof_free(*P);
@@ -925,8 +957,6 @@ exact_status exact_plan_bind_workspace(exact_plan_t plan, void *dev_ptr, size_t 
 
 namespace {
 
-constexpr int kSplitCandidates[] = {1, 2, 3, 4, 6, 8};
-
 struct TuneKey {
     int beam, nx, ny, views, bins;
     bool operator<(const TuneKey &o) const
@@ -955,6 +985,7 @@ exact_status exact_plan_get_tuning(exact_plan_t plan, exact_tuning *out)
 exact_status exact_plan_set_tuning(exact_plan_t plan, const exact_tuning *t)
 {
     if (!plan || !t || t->adj_split < 1 || t->adj_split > kMaxSplit) return EXACT_ERR_INVALID_ARG;
+    if (t->adj_split > reinterpret_cast<Plan *>(plan)->max_split) return EXACT_ERR_UNSUPPORTED;
     reinterpret_cast<Plan *>(plan)->adj_split = t->adj_split;
     return EXACT_OK;
 }
@@ -980,7 +1011,7 @@ exact_status exact_plan_autotune(exact_plan_t plan, int force, exact_tuning *out
     memset(&a, 0, sizeof(a));
     a.rays = P.rays_f;
     a.walk = P.rays_w;
-    a.views = P.views;
+    adj_views(a, P);
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
     a.nx = P.g.nx;
@@ -1004,6 +1035,10 @@ exact_status exact_plan_autotune(exact_plan_t plan, int force, exact_tuning *out
     cudaError_t e = cudaSuccess;
     for (int r = -1; r < kRounds && e == cudaSuccess; ++r)
         for (int c = 0; c < kCands && e == cudaSuccess; ++c) {
+            if (kSplitCandidates[c] > P.max_split) {  // beyond the plan's partial-tile space
+                if (r >= 0) ms[c][r] = INFINITY;
+                continue;
+            }
             a.nsplit = kSplitCandidates[c];
             e = cudaEventRecord(e0, s);
             if (e == cudaSuccess) e = launch_adjoint(a, ADJ_PLAIN, fan, s);
@@ -1070,7 +1105,7 @@ exact_status exact_adjoint(exact_plan_t plan, const float *r, float *g, exact_st
     a.nsplit = P.adj_split;
     a.split_part = P.split_part;
     a.split_count = P.split_count;
-    a.views = P.views;
+    adj_views(a, P);
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
     a.nx = P.g.nx;
@@ -1120,7 +1155,7 @@ exact_status exact_operator(exact_plan_t plan, const float *x, const void *y, ex
     a.nsplit = P.adj_split;
     a.split_part = P.split_part;
     a.split_count = P.split_count;
-    a.views = P.views;
+    adj_views(a, P);
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
     a.nx = P.g.nx;
@@ -1235,7 +1270,7 @@ exact_status exact_solve(exact_plan_t plan, const void *y, exact_dtype y_dtype, 
     a.nsplit = P.adj_split;
     a.split_part = P.split_part;
     a.split_count = P.split_count;
-    a.views = P.views;
+    adj_views(a, P);
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
     a.nx = P.g.nx;
@@ -1472,7 +1507,7 @@ exact_status exact_norm_estimate_f32(exact_plan_t plan, int max_iters, double rt
     a.nsplit = P.adj_split;
     a.split_part = P.split_part;
     a.split_count = P.split_count;
-    a.views = P.views;
+    adj_views(a, P);
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
     a.nx = P.g.nx;
@@ -1767,7 +1802,7 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
         J.f.bg = P.bg_p;
         J.a.rays = P.rays_f;
         J.a.walk = P.rays_w;
-        J.a.views = P.views;
+        adj_views(J.a, P);
         J.a.n_views = P.g.n_views;
         J.a.n_bins = P.g.n_bins;
         J.a.nx = P.g.nx;

@@ -81,8 +81,8 @@ constexpr int kFC = 16;    // driving lines per staged chunk
 constexpr int kFStages = 2;  // staging buffers (copies kFStages - 1 chunks ahead)
 constexpr int kFHB = 192;  // staged cross-axis rows per chunk (tensor-map box height)
 // Adjoint tile (pixels): one CTA gathers A^T r over kTW x kTH pixels.
-constexpr int kTW = 16;
-constexpr int kTH = 16;
+constexpr int kTW = 32;
+constexpr int kTH = 32;
 
 struct __align__(16) FwdUnit {
     int ray0, count, axis, jc0;
@@ -140,6 +140,8 @@ struct Plan {
     float *ray_delta = nullptr;    // [n] step length delta
     RayD *rays_d = nullptr;        // [n]
     ViewRec *views = nullptr;      // [n_views]
+    int *vitems = nullptr;         // [nxv + nyv]: views with x-driven rays, then views with y-driven rays
+    int nxv = 0, nyv = 0;
     // workspace carve-up (all device pointers inside the bound workspace)
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -153,9 +155,10 @@ struct Plan {
     double *tv_lam = nullptr;            // [2] lam carried by the half- and full-step projections
     void *tv_ws = nullptr;               // workspace of the TV-ball projection
     int tv_grid = 0;                     // its cooperative grid
-    float *split_part = nullptr;         // adjoint view split: partial tiles [tiles][kMaxSplit][kTH * kTW]
+    float *split_part = nullptr;         // adjoint view split: partial tiles [tiles][max_split][kTH * kTW]
     int *split_count = nullptr;          // [tiles] arrival counts (zeroed when the workspace is bound)
     int adj_split = 1;                   // CTAs per adjoint tile (exact_plan_autotune / set_tuning)
+    int max_split = 1;                   // largest adj_split the workspace's partial tiles allow
     float *stage_y = nullptr;            // exact_solve_host: device copy of the host counts [W][n]
     float *stage_x = nullptr;            // exact_solve_host: device copy of the host image [d]
     double *xrd = nullptr, *xcd = nullptr;  // FP64 padded copies (power iteration)
@@ -233,6 +236,10 @@ struct AdjArgs {
     const RayF *rays;
     const RayW *walk;
     const ViewRec *views;
+    // the views that have x-driven rays (vitems[0 .. nxv)) and those that
+    // have y-driven rays (vitems[nxv .. nxv + nyv))
+    const int *vitems;
+    int nxv, nyv;
     int n_views, n_bins, nx, ny;
     const float *r;        // [n] residual; already times delta unless `delta` is set
     const float *delta;    // [n] or null: multiply r by delta on the fly
@@ -267,7 +274,16 @@ struct AdjArgs {
     int hist_cap;
 };
 
-constexpr int kMaxSplit = 8;  // view split of the adjoint (autotuned per plan)
+constexpr int kMaxSplit = 16;  // view split of the adjoint (autotuned per plan)
+
+// The plan's view tables in the adjoint's arguments.
+inline void adj_views(AdjArgs &a, const Plan &P)
+{
+    a.views = P.views;
+    a.vitems = P.vitems;
+    a.nxv = P.nxv;
+    a.nyv = P.nyv;
+}
 
 // One job of the persistent multi-job kernel (k_batch.cu).  A round of a job
 // is one extragradient iteration: phase 0 forward+link on x_t (n_units items),

@@ -203,21 +203,34 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
 
 // ------------------------------------------------------------------ adjoint
 
-// Tile kTW x kTH (exact_internal.h).  Each half-warp walks its own views; lane
-// l % 16 of a half owns one tile column (x-driven rays) and one tile row
-// (y-driven rays), so both strips are kTH = kTW pixels long.
-static_assert(kTW == 16 && kTH == 16, "a half-warp covers one tile side");
+// Tile kTW x kTH (exact_internal.h).  A warp walks one view at a time: lane l
+// owns tile column tx0 + l for the x-driven rays and tile row ty0 + l for the
+// y-driven rays, so every strip is kTH = kTW pixels long.  The x-driven parts
+// of all views are gathered first, then the y-driven parts, through the same
+// per-warp accumulator (rows: strip offsets -1 .. kTH; bank = lane).
+static_assert(kTW == 32 && kTH == 32, "a warp covers one tile side");
 constexpr int kRows = kTH + 2;  // accumulator rows: strip offsets -1 .. kTH
 constexpr int kAccLd = 32;      // accumulator row stride: word (row, lane)
 constexpr float kBinEps = 0.01f;
 
 template <int G>
 struct AdjSmem {
-    float acc[G][2][kRows * kAccLd];  // per warp: x-driven then y-driven accumulators
+    union {
+        float acc[G][kRows * kAccLd];  // per warp: its lanes' strips in the current phase
+        float tile[kTH][kTW + 1];      // epilogue (the accumulators are dead by then)
+    };
     float stage[kTH][kTW + 1];
-    float tile[kTH][kTW + 1];
     double red0[G], red1[G], red2[G];
 };
+
+// Hardware reciprocal (MUFU, about 1 ulp); its arguments here are well inside
+// the normal range: 1 + sg e (|sg e| < 1/2) and the positive fan-beam depths.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // Bin range of the rays that cross the segment between two points whose
 // detector projections are (num1/den1, num2/den2) + c, within [lo_bin, hi_bin).
@@ -225,8 +238,8 @@ template <bool FAN>
 __device__ __forceinline__ void seg_range(float num1, float den1, float num2, float den2, float c, int lo_bin,
                                           int hi_bin, int &b0, int &b1)
 {
-    const float u1 = FAN ? __fdividef(num1, den1) : num1;
-    const float u2 = FAN ? __fdividef(num2, den2) : num2;
+    const float u1 = FAN ? num1 * rcp_approx(den1) : num1;
+    const float u2 = FAN ? num2 * rcp_approx(den2) : num2;
     float lo = fminf(u1, u2) + c - kBinEps;
     float hi = fmaxf(u1, u2) + c + kBinEps;
     lo = fminf(fmaxf(lo, -1.0f), (float)hi_bin);
@@ -235,18 +248,18 @@ __device__ __forceinline__ void seg_range(float num1, float den1, float num2, fl
     b1 = min(hi_bin - 1, (int)floorf(hi));
 }
 
-// Walk rays b0..b1 of one view at driving index jf; deposit into acc rows
-// k + 1 and k + 2 (strip offset k = floor(t - kbase) in [-1, kTH - 1]).  The
+// Walk rays b0..b1 of one view at driving index jf; deposit into the lane's
+// pair slot k + 1 (strip offset k = floor(t - kbase) in [-1, kTH - 1]).  The
 // crossing of the middle ray bc is computed from its split record; the others
 // follow from the walk coefficients (RayW) as
 //   t_{bc+e} = t_bc + (kappa e) / (1 + sg e),
 // so a step reads only its residual (and, in a fan, takes one hardware
 // reciprocal).  |e| <= 1/2 of the walk keeps the FP32 error of t within a few
-// 1e-6 pixel (rms about 1e-6).
+// 1e-6 pixel (rms about 1e-6).  al points at the lane's row 0.
 template <bool FAN, bool DELTA, bool COHERENT>
 __device__ __forceinline__ void strip_walk(const RayF *__restrict__ vrays, const RayW *__restrict__ vwalk,
                                            const float *__restrict__ vres, const float *__restrict__ vdelta,
-                                           int b0, int b1, float jf, float kbase, float *__restrict__ acc, int lane)
+                                           int b0, int b1, float jf, float kbase, float *__restrict__ al)
 {
     if (b0 > b1) return;
     const int bc = (b0 + b1) >> 1;
@@ -257,97 +270,88 @@ __device__ __forceinline__ void strip_walk(const RayF *__restrict__ vrays, const
     const float tc = ((q.x - kbase) + p) + (q.y + fmaf(q.w, jf, pe));
     const float kap = fmaf(w.y, jf, w.x);
     float e = (float)(b0 - bc);
-    for (int b = b0; b <= b1; ++b, e += 1.0f) {
-        float rv = ld_dyn<COHERENT>(vres + b);
-        if (DELTA) rv *= __ldg(vdelta + b);
-        const float u = FAN ? fmaf(kap * e, __fdividef(1.0f, fmaf(w.z, e, 1.0f)), tc) : fmaf(kap, e, tc);
+    const float *pr = vres + b0;
+    const float *pd = DELTA ? vdelta + b0 : nullptr;
+#pragma unroll 2
+    for (int n = b1 - b0; n >= 0; --n, e += 1.0f, ++pr) {
+        float rv = ld_dyn<COHERENT>(pr);
+        if (DELTA) rv *= __ldg(pd++);
+        const float u = FAN ? fmaf(kap * e, rcp_approx(fmaf(w.z, e, 1.0f)), tc) : fmaf(kap, e, tc);
         // floor(u) without the conversion pipe (|u| < 2^22)
         const float r = __fadd_rd(u, kFloorMagic);
         const float f = u - (r - kFloorMagic);
-        const int k = __float_as_int(r) - kFloorBias;
-        if ((unsigned)(k + 1) < (unsigned)(kTH + 1)) {
-            const float w1 = f * rv;
-            acc[(k + 1) * kAccLd + lane] += rv - w1;
-            acc[(k + 2) * kAccLd + lane] += w1;
+        // row k + 1 for the strip offset k = floor(u), with the float-to-int bias folded in
+        const unsigned k1 = (unsigned)(__float_as_int(r) - (kFloorBias - 1));
+        if (k1 <= (unsigned)kTH) {
+            float *p = al + k1 * kAccLd;
+            p[0] = fmaf(1.0f - f, rv, p[0]);
+            p[kAccLd] = fmaf(f, rv, p[kAccLd]);
         }
     }
 }
 
 // A^T r over tile (bx, by) with the epilogue of MODE (see k_adjoint.cu).
-// blk is the tile's index (partial norms, split bookkeeping).  The views are
-// split over a.nsplit CTAs (split index z) and, inside one, over its G warps:
-// half-warp q of split z takes views (z G + g) 2 + h + k 2 G nsplit.  With
-// nsplit > 1 each CTA leaves its partial tile in a.split_part; the last of
-// the tile's CTAs to finish (counted in a.split_count, which it resets) adds
-// the partials in split order and runs the epilogue, so the sum is the same
-// on every run.
+// blk is the tile's index (partial norms, split bookkeeping).  Phase 0: warp g
+// of split z walks the x-driven parts of the views a.vitems[it] for
+// it = z G + g + k G nsplit < nxv (lane l: column tx0 + l); phase 1 the
+// y-driven parts of a.vitems[nxv + it], it < nyv (lane l: row ty0 + l).  After
+// each phase the warps' accumulators are added into sm.stage in a fixed
+// order.  With nsplit > 1 each CTA leaves its partial tile in a.split_part;
+// the last of the tile's CTAs to finish (counted in a.split_count, which it
+// resets) adds the partials in split order and runs the epilogue, so the sum
+// is the same on every run.
 template <int MODE, bool FAN, bool DELTA, int G, bool COHERENT>
 __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, long long blk, AdjSmem<G> &sm,
                                              int z = 0)
 {
     __shared__ int s_last;
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5, l = lane & 15;
-    float *accx = sm.acc[g][0];
-    float *accy = sm.acc[g][1];
-    for (int r = 0; r < kRows; ++r) {
-        accx[r * kAccLd + lane] = 0.0f;
-        accy[r * kAccLd + lane] = 0.0f;
-    }
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    float *al = sm.acc[g] + lane;
     const int tx0 = bx * kTW, ty0 = by * kTH;
-    // x-driven strip of this lane: column cx, rows ty0 .. ty0 + kTH - 1
-    const int cx = tx0 + l;
-    const bool xok = cx < a.nx;
-    // strip end points, kept within one pixel of the image so that their
-    // fan-beam projections stay well defined (the source is outside the image)
-    const float fcx = (float)cx, fy_lo = (float)(ty0 - 1), fy_hi = (float)min(ty0 + kTH, a.ny);
-    // y-driven strip of this lane: row ry, columns tx0 .. tx0 + kTW - 1
-    const int ry = ty0 + l;
-    const bool yok = ry < a.ny;
-    const float fry = (float)ry, fx_lo = (float)(tx0 - 1), fx_hi = (float)min(tx0 + kTW, a.nx);
-
     const int nsplit = a.nsplit > 1 ? a.nsplit : 1;
-    for (int v = (z * G + g) * 2 + (lane >> 4); v < a.n_views; v += 2 * G * nsplit) {
-        const ViewRec vr = a.views[v];
-        const long long vb = (long long)v * a.n_bins;
-        const RayF *vrays = a.rays + vb;
-        const RayW *vwalk = a.walk + vb;
-        const float *vres = a.r + vb;
-        const float *vdel = DELTA ? a.delta + vb : nullptr;
-        if (vr.xb1 > vr.xb0 && xok) {
-            const float nb = fmaf(vr.n1, fcx, vr.n0), db = fmaf(vr.d1, fcx, vr.d0);
+    for (int phase = 0; phase < 2; ++phase) {
+        const bool xd = phase == 0;  // uniform: x-driven rays, else y-driven
+        for (int r = 0; r < kRows; ++r) al[r * kAccLd] = 0.0f;
+        // the lane's strip: x-driven rays, column tx0 + lane over rows ty0 ..
+        // ty0 + kTH - 1; y-driven rays, row ty0 + lane over columns tx0 ..
+        // tx0 + kTW - 1.  Its end points are kept within one pixel of the
+        // image so that their fan-beam projections stay well defined (the
+        // source is outside the image).
+        const int line = xd ? tx0 + lane : ty0 + lane;
+        const bool ok = line < (xd ? a.nx : a.ny);
+        const int sb = xd ? ty0 : tx0;
+        const float fl = (float)line, f_lo = (float)(sb - 1), f_hi = (float)min(sb + kTH, xd ? a.ny : a.nx);
+        const int *items = a.vitems + (xd ? 0 : a.nxv);
+        const int nitems = ok ? (xd ? a.nxv : a.nyv) : 0;
+        for (int it = z * G + g; it < nitems; it += G * nsplit) {
+            const int v = __ldg(items + it);
+            const ViewRec vr = a.views[v];
+            const long long vb = (long long)v * a.n_bins;
+            // detector projections of the strip's end points
+            const float nb = xd ? fmaf(vr.n1, fl, vr.n0) : fmaf(vr.n2, fl, vr.n0);
+            const float db = xd ? fmaf(vr.d1, fl, vr.d0) : fmaf(vr.d2, fl, vr.d0);
+            const float na = xd ? vr.n2 : vr.n1, da = xd ? vr.d2 : vr.d1;
             int b0, b1;
-            seg_range<FAN>(fmaf(vr.n2, fy_lo, nb), fmaf(vr.d2, fy_lo, db), fmaf(vr.n2, fy_hi, nb),
-                           fmaf(vr.d2, fy_hi, db), vr.c, vr.xb0, vr.xb1, b0, b1);
-            strip_walk<FAN, DELTA, COHERENT>(vrays, vwalk, vres, vdel, b0, b1, fcx, (float)ty0, accx, lane);
+            seg_range<FAN>(fmaf(na, f_lo, nb), fmaf(da, f_lo, db), fmaf(na, f_hi, nb), fmaf(da, f_hi, db), vr.c,
+                           xd ? vr.xb0 : vr.yb0, xd ? vr.xb1 : vr.yb1, b0, b1);
+            strip_walk<FAN, DELTA, COHERENT>(a.rays + vb, a.walk + vb, a.r + vb, DELTA ? a.delta + vb : nullptr,
+                                             b0, b1, fl, (float)sb, al);
         }
-        if (vr.yb1 > vr.yb0 && yok) {
-            const float nb = fmaf(vr.n2, fry, vr.n0), db = fmaf(vr.d2, fry, vr.d0);
-            int b0, b1;
-            seg_range<FAN>(fmaf(vr.n1, fx_lo, nb), fmaf(vr.d1, fx_lo, db), fmaf(vr.n1, fx_hi, nb),
-                           fmaf(vr.d1, fx_hi, db), vr.c, vr.yb0, vr.yb1, b0, b1);
-            strip_walk<FAN, DELTA, COHERENT>(vrays, vwalk, vres, vdel, b0, b1, fry, (float)tx0, accy, lane);
+        __syncthreads();
+        // fixed-order sum over the warps; pixel j of a lane's strip is its
+        // accumulator row j + 1.  The y-driven parts are read transposed (tile
+        // row = lane) so that consecutive threads read consecutive banks.
+        for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
+            const int i = t % kTW, k = t / kTW;
+            float s = 0.0f;
+            for (int q = 0; q < G; ++q) s += sm.acc[q][(k + 1) * kAccLd + i];
+            if (xd)
+                sm.stage[k][i] = s;   // column i, row k
+            else
+                sm.stage[i][k] += s;  // row i, column k
         }
+        __syncthreads();
     }
-    __syncthreads();
-
-    // fixed-order reduction over the warps and their halves: the y-driven
-    // parts first, staged transposed (row stride kTW + 1), then the x-driven
-    // parts
-    for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
-        const int rl = t % kTH, k = t / kTH;  // tile row rl (y lane), column offset k
-        float s = 0.0f;
-        for (int q = 0; q < G; ++q) s += sm.acc[q][1][(k + 1) * kAccLd + rl] + sm.acc[q][1][(k + 1) * kAccLd + 16 + rl];
-        sm.stage[rl][k] = s;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
-        const int px = t % kTW, py = t / kTW;
-        float gsum = sm.stage[py][px];
-        for (int q = 0; q < G; ++q)
-            gsum += sm.acc[q][0][(py + 1) * kAccLd + px] + sm.acc[q][0][(py + 1) * kAccLd + 16 + px];
-        sm.stage[py][px] = gsum;
-    }
-    __syncthreads();
     if (nsplit > 1) {
         float *mine = a.split_part + ((long long)blk * nsplit + z) * (kTH * kTW);
         for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) mine[t] = sm.stage[t / kTW][t % kTW];

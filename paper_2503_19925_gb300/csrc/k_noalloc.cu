@@ -134,7 +134,7 @@ exact_status exact_operator_static(exact_plan_t plan, const float *x, const void
     memset(&a, 0, sizeof(a));
     a.rays = P.rays_f;
     a.walk = P.rays_w;
-    a.views = P.views;
+    adj_views(a, P);
     a.n_views = P.g.n_views;
     a.n_bins = P.g.n_bins;
     a.nx = P.g.nx;

@@ -115,7 +115,7 @@ def footprint_bytes(geometry: Geometry, W: int, y_itemsize: int) -> int:
     tables = n * (16 + 16 + 4 + 4 + 32) + geometry.n_views * 48 + (n // 16 + 1) * 32 * 8
     ws = 4 * 2 * (geometry.ny * ldr + geometry.nx * ldc) + 8 * n + 8 * (geometry.ny * ldr + geometry.nx * ldc) \
         + 8 * n + 8 * d + 4 * d + (1 << 20) + (13 + 1) * 4 * d + (64 << 10) \
-        + 4 * W * n + 4 * d + 32 * d  # + TV-ball projection buffers, host-buffer staging, view-split partials
+        + 4 * W * n + 4 * d + 64 * d  # + TV-ball projection buffers, host-buffer staging, view-split partials
     return tables + ws + W * n * y_itemsize + 4 * d
 
 

@@ -98,13 +98,20 @@ def test_autotune_picks_a_listed_split_and_caches_it():
     geom = dict(beam=0, nx=96, ny=96, n_views=60, n_bins=137, angle_range=math.pi)
     p1 = ex.Plan(ex.Geometry(**geom), [1.0], [[1.0]])
     t1 = p1.autotune()
-    assert t1["adj_split"] in (1, 2, 3, 4, 6, 8)
+    assert t1["adj_split"] in (1, 2, 3, 4, 6, 8, 12, 16)
     p2 = ex.Plan(ex.Geometry(**geom), [2.0], [[0.5]])
     assert p2.autotune() == t1  # cached shape
     t3 = p2.autotune(force=True)
-    assert t3["adj_split"] in (1, 2, 3, 4, 6, 8)
+    assert t3["adj_split"] in (1, 2, 3, 4, 6, 8, 12, 16)
     with pytest.raises(RuntimeError):
-        p1.set_tuning(9)
+        p1.set_tuning(17)
+    # a large image's limit is below 16 (about 64 CTAs per SM in all)
+    big = ex.Plan(ex.Geometry(beam=0, nx=2048, ny=2048, n_views=8, n_bins=2897, angle_range=math.pi),
+                  [1.0], [[1.0]])
+    with pytest.raises(RuntimeError):
+        big.set_tuning(16)
+    big.set_tuning(2)
+    big.close()
 
 
 def test_batch_autotune_leaves_the_jobs_unchanged():
