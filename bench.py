@@ -58,6 +58,9 @@ def parse_args(argv=None):
     p.add_argument("--cpu-baseline-iters", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-every", type=int, default=10)
+    p.add_argument("--adj-split", type=int, default=0,
+                   help="fix the adjoint's view split instead of autotuning it (0: autotune; profiler runs, "
+                        "whose serialised timings would mislead the autotuner, pass the value it picks)")
     p.add_argument("--no-batched", action="store_true", help="skip the batched-vs-sequential measurement")
     p.add_argument("--batch-jobs", type=int, default=64)
     p.add_argument("--batch-iters", type=int, default=None)
@@ -77,6 +80,10 @@ def parse_args(argv=None):
                    help="arrival rates as fractions of the measured sequential capacity")
     p.add_argument("--serve-mode", choices=["streams", "rounds"], default="streams",
                    help="server mode: each job's solve on its own stream, or persistent-kernel rounds")
+    p.add_argument("--serve-full-jobs", type=int, default=16,
+                   help="requests of a second served stream at the full ranges (0: skip it)")
+    p.add_argument("--serve-full-loads", default="1.5",
+                   help="arrival rates of the full-range stream, as fractions of the sequential capacity")
     return p.parse_args(argv)
 
 
@@ -393,6 +400,8 @@ def run_served(ex, torch, dev, n_jobs: int, loads, rank: int, round_iters: int =
                        "sequential": plain, "speedup_recon_per_s": served["recon_per_s"] / plain["recon_per_s"],
                        "p99_latency_ratio": plain["p99_latency_s"] / served["p99_latency_s"]})
     return {"requests": n_jobs, "sequential_capacity_per_s": cap,
+            "ranges": f"{sc['sizes'][0]}..{sc['sizes'][1]}^2, {sc['views'][0]}..{sc['views'][1]} views, "
+                      f"tol {sc['tol']:g}",
             "workload": f"Poisson stream; {sc['sizes'][0]}..{sc['sizes'][1]}^2, {sc['views'][0]}..{sc['views'][1]} "
                         "views, parallel/fan 50/50, 1..4 windows, 16..64 "
                         f"energies, tol {sc['tol']:g}, HBM budget 150 GB, admission up to {sat_work:g} nonzeros "
@@ -699,7 +708,8 @@ def batched_summary(b: dict) -> dict:
 def served_summary(sv: dict) -> dict:
     """The served leg in a few keys per load: reconstructions/s, p50/p99
     latency and PSNR of the server and of one-at-a-time solves."""
-    out = {"requests": sv["requests"], "capacity_per_s": round(sv["sequential_capacity_per_s"], 3)}
+    out = {"requests": sv["requests"], "ranges": sv["ranges"],
+           "capacity_per_s": round(sv["sequential_capacity_per_s"], 3)}
     for pt in sv["loads"]:
         a, q = pt["served"], pt["sequential"]
         out[f"load_{pt['load_vs_sequential_capacity']:g}"] = {
@@ -731,7 +741,11 @@ def run_exact(args):
     plan = ex.Plan(geom, mu, S)
     plan_ms = 1e3 * (time.perf_counter() - t0)
     t0 = time.perf_counter()
-    tuning = plan.autotune()
+    if args.adj_split > 0:
+        plan.set_tuning(args.adj_split)
+        tuning = dict(plan.tuning)
+    else:
+        tuning = plan.autotune()
     tune_ms = 1e3 * (time.perf_counter() - t0)
     t0 = time.perf_counter()
     normA, norm_iters = plan.norm_estimate(max_iters=500, rtol=1e-9)
@@ -825,6 +839,7 @@ def run_exact(args):
     fwd_avg = fwd_ms / max(fwd_n, 1)
     achieved = nnz / (adj_avg * 1e-3) / 1e9
     traffic = load_traffic("adjoint")
+    traffic_fwd = load_traffic("forward")
     hbm_gbs = float(peaks.get("hbm_gbs", 6686.1))
     roof = {"bound": "alu", "kernel": "k_adjoint (pixel-driven gather + extragradient epilogue)",
             "achieved": achieved, "peak": peak_gnnz, "unit": "Gnnz/s", "frac": achieved / peak_gnnz,
@@ -835,7 +850,8 @@ def run_exact(args):
             "peak_nominal": nominal_gnnz, "frac_of_nominal": achieved / nominal_gnnz,
             "avg_launch_ms": adj_avg, "nnz_per_launch": nnz,
             "forward": {"avg_launch_ms": fwd_avg, "achieved": nnz / (fwd_avg * 1e-3) / 1e9,
-                        "frac": nnz / (fwd_avg * 1e-3) / 1e9 / peak_gnnz},
+                        "frac": nnz / (fwd_avg * 1e-3) / 1e9 / peak_gnnz,
+                        "traffic": traffic_fwd["dram_bytes"] if traffic_fwd else None},
             "kernel_share": {k: v[0] / max(sum(q[0] for q in prof.values()), 1e-12) for k, v in prof.items()},
             "hbm": {"algorithmic_bytes_per_launch": 4 * plan.n_rays + 3 * 4 * geom.nx * geom.ny,
                     "achieved_gbs": (4 * plan.n_rays + 12 * geom.nx * geom.ny) / (adj_avg * 1e-3) / 1e9,
@@ -858,7 +874,7 @@ def run_exact(args):
             "psnr_db": psnr, "eta": eta, "normA_sq": normA, "norm_estimate": {"ms": norm_ms, "iters": norm_iters},
             "plan_create_ms": plan_ms, "tuning": {**tuning, "autotune_ms": tune_ms}}
     # verbose legs first; the compact summaries the headline needs go last
-    batched = served = None
+    batched = served = served_full = None
     if not args.no_tv:
         line["tv"] = run_tv(ex, torch, dev, rank)
     if not args.no_gaussian:
@@ -872,6 +888,11 @@ def run_exact(args):
         served = run_served(ex, torch, dev, args.serve_jobs, [float(v) for v in args.serve_loads.split(",") if v],
                             rank, args.serve_round_iters, args.serve_scale, args.serve_sat_work, args.serve_mode)
         line["served_detail"] = served
+        if args.serve_full_jobs > 0 and args.serve_scale != "full":
+            served_full = run_served(ex, torch, dev, args.serve_full_jobs,
+                                     [float(v) for v in args.serve_full_loads.split(",") if v], rank,
+                                     args.serve_round_iters, "full", args.serve_sat_work, args.serve_mode)
+            line["served_full_detail"] = served_full
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], y_or = cpu_baseline(args.config, args.cpu_baseline_iters)
         line["oracle_parity"] = oracle_parity(ex, torch, dev, args.config, y_or)
@@ -879,6 +900,8 @@ def run_exact(args):
         line["batched"] = batched_summary(batched)
     if served is not None:
         line["served"] = served_summary(served)
+    if served_full is not None:
+        line["served_full"] = served_summary(served_full)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -59,8 +59,8 @@ __device__ __forceinline__ void tma_box(float *dst, const CUtensorMap *map, int 
         : "memory");
 }
 
-template <bool COHERENT>
-__device__ __forceinline__ float ld_dyn(const float *p)
+template <bool COHERENT, typename T>
+__device__ __forceinline__ T ld_dyn(const T *p)
 {
     return COHERENT ? __ldcg(p) : __ldg(p);
 }
@@ -111,7 +111,11 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
     }
     float acc = 0.0f;
     int b = 0;  // stage of chunk c
+    // band start of chunk c, loaded one chunk ahead
+    int ks_next = u.nchunks > 0 ? ld_dyn<COHERENT>(kst) : 0;
     for (int c = 0; c < u.nchunks; ++c) {
+        const int ks = ks_next;
+        if (c + 1 < u.nchunks) ks_next = ld_dyn<COHERENT>(kst + c + 1);
         // every thread waits for chunk c; the barrier then also tells that all
         // threads are done with chunk c - 1, whose buffer the next copy reuses
         bool ok = mbar_wait(&bar[b], (phase >> b) & 1u);
@@ -142,8 +146,8 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
             tma_box(sm.buf[bn], map, kst[cn] + kPad, (u.jc0 + cn) * kFC, &bar[bn]);
         }
         const int j0 = (u.jc0 + c) * kFC;
-        const int ja = max(jlo, j0), jb = min(jhi, j0 + kFC - 1);
-        if (ja <= jb) {
+        // the ray samples this chunk (an empty range, j_lo > j_hi, never does)
+        if (max(jlo, j0) <= min(jhi, j0 + kFC - 1)) {
             // anchor: t(j0) = K + tau0 with tau0 accurate to FP32 rounding at ~1
             const float jf = (float)j0;
             const float p = rec.bh * jf;
@@ -152,23 +156,35 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
             const float tau0 = ((p - P) + rec.a) + fmaf(rec.bl, jf, e);
             // local row = K + floor(tau) - kstart, with the bias of the
             // float-to-int floor folded in
-            const int off = A + (int)P - kst[c] - kFloorBias;
-            const float *sb = sm.buf[b] + (ja - j0) * kFHB;
-            float di = (float)(ja - j0);
-#pragma unroll 4
-            for (int j = ja; j <= jb; ++j) {
-                const float tau = fmaf(rec.bh, di, tau0);
-                // floor(tau) for |tau| < 2^22: a round-down add of 1.5 * 2^23
-                // leaves floor(tau) in the low mantissa bits
-                const float r = __fadd_rd(tau, kFloorMagic);
-                const float f = tau - (r - kFloorMagic);
-                // the host sized the band with a row of margin; the clamp only
-                // keeps a damaged table inside the buffer
-                const int row = min(max(off + __float_as_int(r), 0), kFHB - 2);
-                const float a0 = sb[row], a1 = sb[row + 1];
-                acc += fmaf(f, a1 - a0, a0);
-                sb += kFHB;
-                di += 1.0f;
+            const int off = A + (int)P - ks - kFloorBias;
+            // The walk covers all kFC lines of the chunk, not only the ray's
+            // driving range [jlo, jhi]: outside it the crossing lies beyond the
+            // image by more than a pixel, so both taps read the zero pads or
+            // the copy's zero fill and add exactly +0.  The host sized the band
+            // for the whole chunk; the row is monotone in the line (t is
+            // linear, the round-down floor monotone), so checking the first and
+            // last line keeps every read inside the buffer.  A band that fails
+            // the check (a damaged table) poisons the projection with NaN.
+            const float tl = fmaf(rec.bh, (float)(kFC - 1), tau0);
+            const int rf = off + __float_as_int(__fadd_rd(tau0, kFloorMagic));
+            const int rl = off + __float_as_int(__fadd_rd(tl, kFloorMagic));
+            const bool inside = fabsf(tau0) < 4194304.0f && fabsf(tl) < 4194304.0f &&
+                                (unsigned)rf <= (unsigned)(kFHB - 2) && (unsigned)rl <= (unsigned)(kFHB - 2);
+            if (inside) {
+                const float *sb = sm.buf[b] + off;  // + bits(r) lands in the buffer
+#pragma unroll
+                for (int k = 0; k < kFC; ++k) {
+                    const float tau = fmaf(rec.bh, (float)k, tau0);
+                    // floor(tau) for |tau| < 2^22: a round-down add of 1.5 * 2^23
+                    // leaves floor(tau) in the low mantissa bits
+                    const float r = __fadd_rd(tau, kFloorMagic);
+                    const float f = tau - (r - kFloorMagic);
+                    const float *q = sb + __float_as_int(r) + k * kFHB;
+                    const float a0 = q[0], a1 = q[1];
+                    acc += fmaf(f, a1 - a0, a0);
+                }
+            } else {
+                acc = __int_as_float(0x7fc00000);
             }
         }
         b = b + 1 == kFStages ? 0 : b + 1;

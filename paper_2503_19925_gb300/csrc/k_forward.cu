@@ -23,6 +23,14 @@
 // stays small, so FP32 keeps t to ~1e-6 pixel at any image size (a plain
 // fmaf(beta, j, alpha) loses ~3e-5 pixel at 512).
 //
+// Every ray that samples a chunk walks all kFC of its lines in a fully
+// unrolled loop (line offset a compile-time constant, no per-line range test
+// or clamp): lines outside the ray's driving range put its crossing more than
+// a pixel outside the image, where both taps read zeros, so the sum is the
+// same bit for bit as a walk over the range alone.  The band rows of the
+// chunk's first and last line are checked once; the row is monotone in the
+// line, so that bounds every read.
+//
 // Link epilogue: r_i = delta_i (Y_i - sum_k c_k 2^(-mu2_k max(z_i, 0))) with
 // c_k = I0 sum_w S[w][k] and Y_i = sum_w y[w][i] (F is linear in y, so summing
 // the windows first is exact algebra); the per-energy coefficients live in the
