@@ -397,7 +397,7 @@ exact_status exact_recommended_eta(exact_plan_t plan, double I0, double normA_sq
  *    device current) and keeps it; make that first call before any stream
  *    capture.  cudaDeviceReset invalidates the kept address: do not call this
  *    entry point again in a process that reset the device.
- *  - The adjoint runs one CTA per 16 x 16 tile whatever the plan's
+ *  - The adjoint runs one CTA per 32 x 32 tile whatever the plan's
  *    exact_tuning.adj_split (a split needs the workspace), so F equals
  *    exact_operator's up to the FP32 summation order when adj_split > 1.
  *  - Every call shares the array and it keeps the last call's contents (each

@@ -4,31 +4,35 @@
 // stopping rule.
 //
 // FP32 kernel (hot path, body in joseph.cuh): one CTA owns a tile of kTW x kTH
-// (16 x 16) pixels; its kG warps split the views by half-warp (half-warp q
-// takes views q, q + 2 kG, ...; interleaving keeps the loads even).  For each
-// view a half-warp walks the rays that cross the tile:
-//   - x-driven rays sample every pixel column; lane l (of 16) owns column
-//     tx0 + l and walks, in bin order, the rays whose crossing with that
-//     column lies strictly inside (ty0 - 1, ty0 + kTH).  Each ray adds
-//     (1 - f) r and f r to the two pixels around its crossing (the two nonzero
-//     entries of its row of A in this column);
-//   - y-driven rays sample every pixel row; lane l owns row ty0 + l and walks
-//     its rays the same way.
+// (32 x 32) pixels and, with a view split, one of its nsplit view subsets.  Its
+// kG warps take one view at a time from the plan's view lists, in two phases:
+//   - x-driven rays sample every pixel column; lane l owns column tx0 + l and
+//     walks, in bin order, the rays whose crossing with that column lies
+//     strictly inside (ty0 - 1, ty0 + kTH).  Each ray adds (1 - f) r and f r
+//     to the two pixels around its crossing (the two nonzero entries of its
+//     row of A in this column);
+//   - then the views with y-driven rays: lane l owns row ty0 + l and walks its
+//     rays the same way.
+// Warp g of split z takes items z kG + g + k kG nsplit of each list, so the
+// splits interleave over the views.
 // The rays crossing a strip form one contiguous bin range: the two end points
 // of the strip projected onto the detector (a ratio of affine forms of the
 // pixel coordinates, stored per view) bound it.  Each lane accumulates into
-// its own column of a warp-private shared-memory array (bank = lane: no
-// conflicts, no races); at the end the CTA adds the warps' arrays in a fixed
-// order.  Every output is therefore the same fixed-order sum on every run.
+// its own column of a warp-private [kTH + 2][32] shared-memory array (bank =
+// lane: no conflicts, no races); after each phase the CTA adds the warps'
+// arrays into the tile in a fixed order (the y phase transposed).  With a view
+// split, the last of a tile's CTAs adds the partial tiles in split order.
+// Every output is therefore the same fixed-order sum on every run.
 //
 // Ray coordinates: the crossing of the middle ray of a walk comes from the
 // split FP32 record of k_forward.cu (exact product split, exact cancellation
 // of the large terms); the other rays of the walk follow from per-ray walk
 // coefficients, t_{b+e} = t_b + kappa e / (1 + sg e) (exact for both beams:
 // the crossing is a Moebius function of the bin index), so a step reads one
-// residual and no ray record.  The interpolation weights match the FP64
-// matrix to ~1e-6 and the gather is the transpose of the forward walk up to
-// FP32 rounding.
+// residual and no ray record, and costs one hardware reciprocal.  The
+// interpolation weights match the FP64 matrix to ~1e-6 and the gather is the
+// transpose of the forward walk up to FP32 rounding (its crossings agree with
+// the forward's per-line anchors to ~1e-6 pixel, not bit for bit).
 //
 // FP64 kernel (power iteration, once per plan): one thread per pixel loops over
 // the views and evaluates the few candidate rays of each view directly.
@@ -38,7 +42,7 @@ namespace exact {
 
 namespace {
 
-constexpr int kG = 6;  // warps per CTA of the per-plan kernel (2 kG view subsets)
+constexpr int kG = 6;  // warps per CTA of the per-plan kernel (one view at a time each)
 
 template <int MODE, bool FAN, bool DELTA>
 __global__ void __launch_bounds__(kG * 32, 7) k_adjoint(AdjArgs a)
