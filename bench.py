@@ -601,11 +601,18 @@ def run_gaussian(ex, torch, dev):
                         "step 0.25, no projection, FP64", "max_iters": max_iters, "points": out}
 
 
+BATCH_POLICIES = ("persistent kernel, one CTA per tile", "persistent kernel, per-plan adj_split",
+                  "one exact_solve per job on 8 streams")
+
+
 def run_batched(ex, torch, dev, n_jobs: int, iters: int, rank: int):
     """The batched mix: n_jobs reconstructions of uneven size/views/windows,
-    (a) one after another with exact_solve, (b) in one persistent launch with
-    exact_batch_solve, (c) the same batch replayed from a captured CUDA graph.
-    Returns reconstructions/s, latencies and mean PSNR of each."""
+    (a) one after another with exact_solve, (b) in one exact_batch_solve call
+    under each batch policy -- 0 and 1: one persistent launch for all jobs
+    (one CTA per adjoint tile / each plan's split), 2: every job's own
+    exact_solve on one of the context's eight streams -- and under the policy
+    exact_batch_autotune picks, (c) that call replayed from a captured CUDA
+    graph.  Returns reconstructions/s, latencies and mean PSNR of each."""
     specs = configs.c4_jobs(n_jobs=n_jobs)
     jobs_in = [make_job_inputs(ex, torch, sp, dev, rank) for sp in specs]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -661,6 +668,12 @@ def run_batched(ex, torch, dev, n_jobs: int, iters: int, rank: int):
 
     seq_ms, seq_lat = timed(seq_pass)
     psnr_seq = psnr_of(xs_seq)
+    pol = {}
+    for pp, name in enumerate(BATCH_POLICIES):
+        batch.set_policy(pp)
+        ms_p, _ = timed(batch_pass)
+        pol[name] = {"recon_per_s": n_jobs / (ms_p / 1e3), "ms": ms_p, "mean_psnr_db": psnr_of(xs_b)}
+    batch.set_policy(policy)
     b_ms, _ = timed(batch_pass)
     psnr_b = psnr_of(xs_b)
     # graph capture of the whole batched call (zeroing the iterates included)
@@ -683,8 +696,9 @@ def run_batched(ex, torch, dev, n_jobs: int, iters: int, rank: int):
         "batched": {"recon_per_s": n_jobs / (b_ms / 1e3), "ms": b_ms, "p50_latency_ms": b_ms, "p99_latency_ms": b_ms,
                     "mean_psnr_db": psnr_b},
         "batched_graph": {"recon_per_s": n_jobs / (g_ms / 1e3), "ms": g_ms, "mean_psnr_db": psnr_g},
+        "policies": pol,
         "speedup_vs_sequential": seq_ms / b_ms,
-        "tuning": {"batch_split_policy": ["one CTA per tile", "per-plan adj_split"][policy],
+        "tuning": {"batch_policy": BATCH_POLICIES[policy],
                    "plan_adj_splits": sorted({p.tuning["adj_split"] for p, _, _, _ in jobs_in})}}
     batch.close()
     for p, _, _, _ in jobs_in:
@@ -696,9 +710,10 @@ def batched_summary(b: dict) -> dict:
     """The batched leg in a few keys: reconstructions/s of each form, latency,
     PSNR, speed-up over one-at-a-time solves."""
     s, p, g = b["sequential"], b["batched"], b["batched_graph"]
-    return {"jobs": b["jobs"], "iters": b["iters_per_job"],
+    return {"jobs": b["jobs"], "iters": b["iters_per_job"], "policy": b["tuning"]["batch_policy"],
             "recon_per_s": {"sequential": round(s["recon_per_s"], 2), "batched": round(p["recon_per_s"], 2),
-                            "graph": round(g["recon_per_s"], 2)},
+                            "graph": round(g["recon_per_s"], 2),
+                            "per_policy": [round(v["recon_per_s"], 2) for v in b["policies"].values()]},
             "p50_p99_ms": {"sequential": [round(s["p50_latency_ms"], 1), round(s["p99_latency_ms"], 1)],
                            "batched": [round(p["p50_latency_ms"], 1), round(p["p99_latency_ms"], 1)]},
             "psnr_db": {"sequential": round(s["mean_psnr_db"], 3), "batched": round(p["mean_psnr_db"], 3)},

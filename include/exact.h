@@ -449,29 +449,40 @@ exact_status exact_batch_create(int max_jobs, exact_batch_t *out);
 /* Free a batch context (no work using it may be in flight). */
 exact_status exact_batch_destroy(exact_batch_t batch);
 
-/* Run the projected extragradient iteration of every job in one persistent
- * kernel launch: the work of all jobs (forward units, adjoint tiles,
- * reductions of each iteration) is handed out in a fixed order through a
- * device work counter; an item waits (bounded spin, then EXACT_ERR_TIMEOUT)
- * only for the previous phase of its own job, so different jobs overlap.
- * Per job the arithmetic is the same for any batch composition, so a job's
- * result does not depend on the other jobs.  Jobs on one call must be
- * distinct plans on the current device.  Asynchronous on `stream` (set-up
- * kernels, one persistent launch, result copies); capturable in a CUDA graph.
- * The context's staging is reused by the next call, which waits for this call's
- * staging copy first. */
+/* Run the projected extragradient iteration (Eq. (11)) of every job.  Under
+ * the context's policy 0 or 1 (exact_batch_autotune, exact_batch_set_policy)
+ * all jobs run in one persistent kernel launch: the work of all jobs (forward
+ * units, adjoint tiles, reductions of each iteration) is handed out in a fixed
+ * order through a device work counter; an item waits (bounded spin, then
+ * EXACT_ERR_TIMEOUT) only for the previous phase of its own job, so different
+ * jobs overlap.  Under policy 2 each job runs as its own exact_solve (graph
+ * loop, the plan's adj_split) on one of the context's 8 streams, round robin,
+ * forked from and joined back into `stream` with events, so jobs overlap
+ * through the streams.  Per job the arithmetic is the same for any batch
+ * composition, so a job's result does not depend on the other jobs (under
+ * policy 2 it equals exact_solve's bit for bit).  Jobs on one call must be
+ * distinct plans on the current device.  Asynchronous on `stream`;
+ * capturable in a CUDA graph.  The context's staging is reused by the next
+ * call, which waits for this call's staging copy first. */
 exact_status exact_batch_solve(exact_batch_t batch, const exact_job *jobs, int n_jobs, exact_stream_t stream);
 
 /* Autotuner of a batch context (no counterpart in the paper): times
  * exact_batch_solve on these jobs, two iterations each (best of two after a
- * warm-up run), under each adjoint split policy -- 0: one CTA per adjoint
- * tile; 1: each plan's own exact_tuning.adj_split -- and keeps the faster one
- * (policy 1 only when more than 3% faster) for later exact_batch_solve calls
- * of this context.  Every job's x is saved in its plan's workspace and
+ * warm-up run), under each policy -- 0: persistent kernel, one CTA per
+ * adjoint tile; 1: persistent kernel, each plan's own exact_tuning.adj_split;
+ * 2: one exact_solve per job on the context's streams -- and keeps the
+ * fastest (a later policy only when more than 3% faster) for later
+ * exact_batch_solve calls of this context.  Every job's x is saved in its plan's workspace and
  * restored after each trial, and the jobs' info structs are not written.
  * policy_out may be NULL.  Synchronises. */
 exact_status exact_batch_autotune(exact_batch_t batch, const exact_job *jobs, int n_jobs, int *policy_out,
                                   exact_stream_t stream);
+
+/* Set or read a batch context's policy (0, 1 or 2, as exact_batch_autotune;
+ * a new context starts at 0).  No counterpart in the paper.  Set returns
+ * EXACT_ERR_INVALID_ARG for another value. */
+exact_status exact_batch_set_policy(exact_batch_t batch, int policy);
+exact_status exact_batch_get_policy(exact_batch_t batch, int *policy);
 
 /* Number of nonzero entries of A (pairs of ray and pixel with a positive
  * Joseph weight), counted in FP64 on the host at plan creation: the

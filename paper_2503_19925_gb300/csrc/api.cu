@@ -1676,8 +1676,13 @@ struct exact_batch {
     cudaEvent_t staged = nullptr;
     bool staged_pending = false;
     int grid = 0;
-    int split_policy = 0;  // 0: one CTA per adjoint tile; 1: each plan's adj_split (exact_batch_autotune)
+    // 0: persistent kernel, one CTA per adjoint tile; 1: persistent kernel,
+    // each plan's adj_split; 2: each job's exact_solve on one of `streams`
+    // (exact_batch_autotune / exact_batch_set_policy)
+    int split_policy = 0;
     std::vector<void *> captured_infos;  // info payloads of captured graphs
+    cudaStream_t streams[kBatchStreams] = {};
+    cudaEvent_t fork = nullptr, joins[kBatchStreams] = {};
 };
 
 extern "C" {
@@ -1701,6 +1706,11 @@ exact_status exact_batch_create(int max_jobs, exact_batch_t *out)
     if (e == cudaSuccess) e = cudaMalloc(&B->dev, B->L.total);
     if (e == cudaSuccess) e = cudaMalloc(&B->counters, B->counter_bytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->staged, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+    for (int k = 0; k < kBatchStreams && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&B->streams[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->joins[k], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         exact_batch_destroy(B);
         return cuda_status(e);
@@ -1719,6 +1729,11 @@ exact_status exact_batch_destroy(exact_batch_t B)
 {
     if (!B) return EXACT_OK;
     if (B->staged) cudaEventDestroy(B->staged);
+    if (B->fork) cudaEventDestroy(B->fork);
+    for (int k = 0; k < kBatchStreams; ++k) {
+        if (B->joins[k]) cudaEventDestroy(B->joins[k]);
+        if (B->streams[k]) cudaStreamDestroy(B->streams[k]);
+    }
     for (void *c : B->captured_infos) delete static_cast<InfoCopy *>(c);
     if (B->host) cudaFreeHost(B->host);
     if (B->dev) cudaFree(B->dev);
@@ -1753,6 +1768,28 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
         for (int q = 0; q < j; ++q)
             if (jobs[q].plan == J.plan) return EXACT_ERR_INVALID_ARG;
         rounds = J.iters > rounds ? J.iters : rounds;
+    }
+    if (B->split_policy == 2) {
+        // each job's own solve (its graph loop and adj_split) on one of the
+        // context's streams, round robin; forked from and joined back into
+        // `stream` with events, so the call stays ordered on `stream` (and
+        // capturable).  Each job's arithmetic is that of exact_solve.
+        const int K = n_jobs < kBatchStreams ? n_jobs : kBatchStreams;
+        EXACT_TRY(cudaEventRecord(B->fork, s));
+        for (int k = 0; k < K; ++k) EXACT_TRY(cudaStreamWaitEvent(B->streams[k], B->fork, 0));
+        exact_status st = EXACT_OK;
+        for (int j = 0; j < n_jobs && st == EXACT_OK; ++j) {
+            const exact_job &J = jobs[j];
+            st = exact_solve(J.plan, J.y, J.y_dtype, J.I0, J.eta, J.iters, &J.opts, J.x, J.info,
+                             reinterpret_cast<exact_stream_t>(B->streams[j % K]));
+        }
+        // join every forked stream, also after a failed call
+        for (int k = 0; k < K; ++k) {
+            const cudaError_t e = cudaEventRecord(B->joins[k], B->streams[k]);
+            const cudaError_t w = e == cudaSuccess ? cudaStreamWaitEvent(s, B->joins[k], 0) : e;
+            if (w != cudaSuccess && st == EXACT_OK) st = cuda_status(w);
+        }
+        return st;
     }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     EXACT_TRY(cudaStreamIsCapturing(s, &cap));
@@ -1880,6 +1917,20 @@ exact_status exact_batch_solve(exact_batch_t B, const exact_job *jobs, int n_job
 }
 
 
+exact_status exact_batch_set_policy(exact_batch_t B, int policy)
+{
+    if (!B || policy < 0 || policy > 2) return EXACT_ERR_INVALID_ARG;
+    B->split_policy = policy;
+    return EXACT_OK;
+}
+
+exact_status exact_batch_get_policy(exact_batch_t B, int *policy)
+{
+    if (!B || !policy) return EXACT_ERR_INVALID_ARG;
+    *policy = B->split_policy;
+    return EXACT_OK;
+}
+
 exact_status exact_batch_autotune(exact_batch_t B, const exact_job *jobs, int n_jobs, int *policy_out,
                                   exact_stream_t stream)
 {
@@ -1908,7 +1959,7 @@ exact_status exact_batch_autotune(exact_batch_t B, const exact_job *jobs, int n_
     float best_ms = INFINITY;
     int best = 0;
     exact_status st = EXACT_OK;
-    for (int policy = 0; policy < 2 && st == EXACT_OK; ++policy) {
+    for (int policy = 0; policy < 3 && st == EXACT_OK; ++policy) {
         B->split_policy = policy;
         float ms_min = INFINITY;
         for (int rep = 0; rep < 3 && st == EXACT_OK; ++rep) {

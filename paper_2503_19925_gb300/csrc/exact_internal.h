@@ -314,6 +314,7 @@ bool debug_take_tv_block();    // block the next TV launch's grid barrier
 
 constexpr int kBatchThreads = 128;  // = kFR, and 4 adjoint warps
 constexpr int kMaxBatch = 256;      // jobs per batch launch
+constexpr int kBatchStreams = 8;    // streams of a batch context (policy 2: one solve per stream at a time)
 
 // ---- host helpers shared by the plan code (api.cu) and exact_operator_static --
 // 2D tensor map of one padded image copy (box kFHB x kFC, zero fill outside).

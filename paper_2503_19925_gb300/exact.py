@@ -131,6 +131,8 @@ _SIGS = [
     ("exact_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_VP)]),
     ("exact_batch_destroy", ctypes.c_int, [_VP]),
     ("exact_batch_solve", ctypes.c_int, [_VP, ctypes.POINTER(_Job), ctypes.c_int, _VP]),
+    ("exact_batch_set_policy", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("exact_batch_get_policy", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     ("exact_batch_autotune", ctypes.c_int, [_VP, ctypes.POINTER(_Job), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                             _VP]),
     ("exact_profile_enable", ctypes.c_int, [_VP, ctypes.c_int]),
@@ -602,7 +604,9 @@ class Job:
 
 
 class Batch:
-    """Persistent multi-job solver context (exact_batch_*)."""
+    """Multi-job solver context (exact_batch_*): policy 0 or 1 runs all jobs in
+    one persistent kernel launch, policy 2 each job's own solve on one of the
+    context's streams (see `autotune`, `set_policy`)."""
 
     def __init__(self, max_jobs: int = 64):
         lib = load()
@@ -642,8 +646,20 @@ class Batch:
                           x.data_ptr(), ctypes.pointer(infos[k]))
         return arr, infos, xs
 
+    @property
+    def policy(self) -> int:
+        v = ctypes.c_int(0)
+        _check("exact_batch_get_policy", load().exact_batch_get_policy(self._h, ctypes.byref(v)))
+        return v.value
+
+    def set_policy(self, policy: int):
+        """0: persistent kernel, one CTA per adjoint tile; 1: persistent kernel,
+        each plan's adj_split; 2: each job's exact_solve on the context's
+        streams (exact_batch_set_policy)."""
+        _check("exact_batch_set_policy", load().exact_batch_set_policy(self._h, int(policy)))
+
     def autotune(self, jobs: list[Job]) -> int:
-        """Pick this context's adjoint split policy by timing these jobs
+        """Pick this context's policy (0, 1 or 2) by timing these jobs
         (exact_batch_autotune; the jobs' images are left as they were)."""
         arr, _, _ = self._jobs(jobs)
         policy = ctypes.c_int(0)
@@ -652,8 +668,9 @@ class Batch:
         return policy.value
 
     def solve(self, jobs: list[Job], sync: bool = True):
-        """Run all jobs in one persistent launch; returns the list of SolveInfo
-        (filled once the stream passes the end of the batch) and the images."""
+        """Run all jobs (one persistent launch, or one solve per job on the
+        context's streams under policy 2); returns the images and the list of
+        SolveInfo (filled once the stream passes the end of the batch)."""
         n = len(jobs)
         arr, infos, xs = self._jobs(jobs)
         _check("exact_batch_solve", load().exact_batch_solve(self._h, arr, n, _stream()))

@@ -1,6 +1,8 @@
-"""Batched solves (one persistent launch for many jobs) against single solves
-and the oracle: a job's result is bitwise the same alone and in any mix, and
-matches the single-job path and the FP64 oracle within the solve tolerances."""
+"""Batched solves against single solves and the oracle, under policy 0 (one
+persistent launch for all jobs) and policy 2 (each job's own solve on one of
+the batch context's streams): a job's result is bitwise the same alone and in
+any mix, matches the single-job path (bit for bit under policy 2) and the FP64
+oracle within the solve tolerances, and replays from a captured CUDA graph."""
 import math
 
 import pytest
@@ -50,12 +52,25 @@ def _jobs(mix, iters, idx=None, **kw):
                    iters=iters[k] if isinstance(iters, (list, tuple)) else iters, **kw) for k in idx]
 
 
-def test_batch_matches_single_solve_and_oracle(mix):
-    batch = ex.Batch(8)
+POLICIES = [0, 2]
+
+
+def _batch(n, policy):
+    b = ex.Batch(n)
+    b.set_policy(policy)
+    assert b.policy == policy
+    return b
+
+
+@pytest.mark.parametrize("policy", POLICIES)
+def test_batch_matches_single_solve_and_oracle(mix, policy):
+    batch = _batch(8, policy)
     xs, infos = batch.solve(_jobs(mix, 12))
     for k, (p, plan, y, eta) in enumerate(mix):
         single, _ = plan.solve(y, p["I0"], eta, 12)
         assert rel_l2(xs[k].double().cpu().numpy(), single.double().cpu().numpy()) <= 1e-5
+        if policy == 2:
+            assert torch.equal(xs[k], single)
         ref = oracle.solve(p["g_or"], p["S"], p["mu"], p["I0"], p["y"], eta, 12)
         xb = xs[k].double().cpu().numpy()
         assert rel_l2(xb, ref.x) <= 1e-3
@@ -64,8 +79,9 @@ def test_batch_matches_single_solve_and_oracle(mix):
     batch.close()
 
 
-def test_result_independent_of_mix(mix):
-    batch = ex.Batch(8)
+@pytest.mark.parametrize("policy", POLICIES)
+def test_result_independent_of_mix(mix, policy):
+    batch = _batch(8, policy)
     iters = [9, 14, 5, 11, 7]
     xs_all, infos_all = batch.solve(_jobs(mix, iters))
     for k in range(len(mix)):
@@ -78,8 +94,9 @@ def test_result_independent_of_mix(mix):
     batch.close()
 
 
-def test_batch_tolerance_stop_and_box(mix):
-    batch = ex.Batch(8)
+@pytest.mark.parametrize("policy", POLICIES)
+def test_batch_tolerance_stop_and_box(mix, policy):
+    batch = _batch(8, policy)
     p, plan, y, eta = mix[0]
     full = oracle.solve(p["g_or"], p["S"], p["mu"], p["I0"], p["y"], eta, 150)
     tol = float(full.rel_res[40])
@@ -91,8 +108,9 @@ def test_batch_tolerance_stop_and_box(mix):
     batch.close()
 
 
-def test_batch_in_cuda_graph(mix):
-    batch = ex.Batch(8)
+@pytest.mark.parametrize("policy", POLICIES)
+def test_batch_in_cuda_graph(mix, policy):
+    batch = _batch(8, policy)
     jobs = _jobs(mix, 6)
     xs_ref, _ = batch.solve(jobs)
     ref = [x.clone() for x in xs_ref]
@@ -115,8 +133,19 @@ def test_batch_in_cuda_graph(mix):
     batch.close()
 
 
-def test_batch_invalid_arguments(mix):
+def test_batch_policy_argument():
     batch = ex.Batch(2)
+    assert batch.policy == 0  # a new context runs the persistent kernel
+    for bad in (-1, 3):
+        with pytest.raises(ex.ExactError):
+            batch.set_policy(bad)
+    assert batch.policy == 0
+    batch.close()
+
+
+@pytest.mark.parametrize("policy", POLICIES)
+def test_batch_invalid_arguments(mix, policy):
+    batch = _batch(2, policy)
     with pytest.raises(ex.ExactError):  # more jobs than the context holds
         batch.solve(_jobs(mix, 3))
     with pytest.raises(ex.ExactError):  # the same plan twice

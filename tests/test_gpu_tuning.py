@@ -129,7 +129,8 @@ def test_batch_autotune_leaves_the_jobs_unchanged():
     before = [j.x.clone() for j in jobs_in]
     batch = ex.Batch(4)
     policy = batch.autotune(jobs_in)
-    assert policy in (0, 1)
+    assert policy in (0, 1, 2)
+    assert batch.policy == policy
     for j, b in zip(jobs_in, before):
         assert torch.equal(j.x, b)
     batch.close()
