@@ -240,15 +240,28 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
 // y-driven rays, so every strip is kTH = kTW pixels long.  The x-driven parts
 // of all views are gathered first, then the y-driven parts, through the same
 // per-warp accumulator (rows: strip offsets -1 .. kTH; bank = lane).
+//
+// Fan beams in the per-plan kernel walk line pairs instead: lane l owns the
+// driving lines 2 (l % 16) and 2 (l % 16) + 1 over half h = l / 16 of the cross
+// axis (kHalf pixels), so one step along a ray (residual load, reciprocal,
+// loop) serves two crossings.  Each half has its own accumulator of kRowsH
+// rows (strip offsets -1 .. kHalf) by 32 words; lane l keeps its two lines in
+// words (2 (l % 16) + d + h) mod 32, d = 0, 1, so that the 32 lanes of a
+// deposit touch 32 different banks.  As at tile edges, a crossing between the
+// halves is walked by both, each keeping only its own pixels' weights.
 static_assert(kTW == 32 && kTH == 32, "a warp covers one tile side");
 constexpr int kRows = kTH + 2;  // accumulator rows: strip offsets -1 .. kTH
 constexpr int kAccLd = 32;      // accumulator row stride: word (row, lane)
+constexpr int kHalf = kTH / 2;                  // line pairs: strip length
+constexpr int kRowsH = kHalf + 2;               // line pairs: rows per half (strip offsets -1 .. kHalf)
+constexpr int kHalfWords = kRowsH * kAccLd;     // line pairs: words per half
+constexpr int kAccWords = 2 * kHalfWords > kRows * kAccLd ? 2 * kHalfWords : kRows * kAccLd;
 constexpr float kBinEps = 0.01f;
 
 template <int G>
 struct AdjSmem {
     union {
-        float acc[G][kRows * kAccLd];  // per warp: its lanes' strips in the current phase
+        float acc[G][kAccWords];       // per warp: its lanes' strips in the current phase
         float tile[kTH][kTW + 1];      // epilogue (the accumulators are dead by then)
     };
     float stage[kTH][kTW + 1];
@@ -322,6 +335,73 @@ __device__ __forceinline__ void strip_walk(const RayF *__restrict__ vrays, const
     }
 }
 
+// Bin range of the rays that cross either of two adjacent lines between cross
+// coordinates f_lo and f_hi: the hull of the detector projections
+// (num/den + c) of the four corners, within [lo_bin, hi_bin).
+template <bool FAN>
+__device__ __forceinline__ void seg_range2(float n00, float d00, float n01, float d01, float n10, float d10,
+                                           float n11, float d11, float c, int lo_bin, int hi_bin, int &b0, int &b1)
+{
+    const float u00 = FAN ? n00 * rcp_approx(d00) : n00, u01 = FAN ? n01 * rcp_approx(d01) : n01;
+    const float u10 = FAN ? n10 * rcp_approx(d10) : n10, u11 = FAN ? n11 * rcp_approx(d11) : n11;
+    float lo = fminf(fminf(u00, u01), fminf(u10, u11)) + c - kBinEps;
+    float hi = fmaxf(fmaxf(u00, u01), fmaxf(u10, u11)) + c + kBinEps;
+    lo = fminf(fmaxf(lo, -1.0f), (float)hi_bin);
+    hi = fminf(fmaxf(hi, -1.0f), (float)hi_bin);
+    b0 = max(lo_bin, (int)ceilf(lo));
+    b1 = min(hi_bin - 1, (int)floorf(hi));
+}
+
+// One crossing of a half strip: t relative to the strip's first pixel, strip
+// offset k = floor(t) in [-1, kHalf - 1] deposited into rows k + 1 and k + 2
+// (al points at row 0); other crossings belong to other strips.
+__device__ __forceinline__ void deposit_half(float *__restrict__ al, float t, float rv)
+{
+    const float r = __fadd_rd(t, kFloorMagic);
+    const float f = t - (r - kFloorMagic);
+    const unsigned k1 = (unsigned)(__float_as_int(r) - (kFloorBias - 1));
+    if (k1 <= (unsigned)kHalf) {
+        float *p = al + k1 * kAccLd;
+        p[0] = fmaf(1.0f - f, rv, p[0]);
+        p[kAccLd] = fmaf(f, rv, p[kAccLd]);
+    }
+}
+
+// Line-pair walk (fan beam): rays b0..b1 of one view across driving lines jf
+// and jf + 1, into the lane's two half strips (al0: line jf, al1: line jf + 1).
+// The crossings of the middle ray bc come from its split record, the others
+// from t_{bc+e} = t_bc + kappa (e / (1 + sg e)), where only t_bc and kappa
+// depend on the line: one step reads one residual and takes one reciprocal
+// for both crossings.
+template <bool DELTA, bool COHERENT>
+__device__ __forceinline__ void strip_walk2(const RayF *__restrict__ vrays, const RayW *__restrict__ vwalk,
+                                            const float *__restrict__ vres, const float *__restrict__ vdelta,
+                                            int b0, int b1, float jf, float kbase, float *__restrict__ al0,
+                                            float *__restrict__ al1)
+{
+    if (b0 > b1) return;
+    const int bc = (b0 + b1) >> 1;
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(vrays + bc));
+    const float4 w = __ldg(reinterpret_cast<const float4 *>(vwalk + bc));
+    const float jg = jf + 1.0f;
+    const float p0 = q.z * jf, p1 = q.z * jg;
+    const float pe0 = fmaf(q.z, jf, -p0), pe1 = fmaf(q.z, jg, -p1);
+    const float tc0 = ((q.x - kbase) + p0) + (q.y + fmaf(q.w, jf, pe0));
+    const float tc1 = ((q.x - kbase) + p1) + (q.y + fmaf(q.w, jg, pe1));
+    const float kap0 = fmaf(w.y, jf, w.x), kap1 = fmaf(w.y, jg, w.x);
+    float e = (float)(b0 - bc);
+    const float *pr = vres + b0;
+    const float *pd = DELTA ? vdelta + b0 : nullptr;
+#pragma unroll 2
+    for (int n = b1 - b0; n >= 0; --n, e += 1.0f, ++pr) {
+        float rv = ld_dyn<COHERENT>(pr);
+        if (DELTA) rv *= __ldg(pd++);
+        const float qe = e * rcp_approx(fmaf(w.z, e, 1.0f));
+        deposit_half(al0, fmaf(kap0, qe, tc0), rv);
+        deposit_half(al1, fmaf(kap1, qe, tc1), rv);
+    }
+}
+
 // A^T r over tile (bx, by) with the epilogue of MODE (see k_adjoint.cu).
 // blk is the tile's index (partial norms, split bookkeeping).  Phase 0: warp g
 // of split z walks the x-driven parts of the views a.vitems[it] for
@@ -338,49 +418,99 @@ __device__ __forceinline__ void adjoint_tile(const AdjArgs &a, int bx, int by, l
 {
     __shared__ int s_last;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    float *al = sm.acc[g] + lane;
     const int tx0 = bx * kTW, ty0 = by * kTH;
     const int nsplit = a.nsplit > 1 ? a.nsplit : 1;
+    // line pairs for fan beams in the per-plan kernel (see kHalf); the
+    // persistent kernel keeps one walk for all its jobs
+    constexpr bool PAIR = FAN && !COHERENT;
     for (int phase = 0; phase < 2; ++phase) {
         const bool xd = phase == 0;  // uniform: x-driven rays, else y-driven
-        for (int r = 0; r < kRows; ++r) al[r * kAccLd] = 0.0f;
-        // the lane's strip: x-driven rays, column tx0 + lane over rows ty0 ..
-        // ty0 + kTH - 1; y-driven rays, row ty0 + lane over columns tx0 ..
-        // tx0 + kTW - 1.  Its end points are kept within one pixel of the
-        // image so that their fan-beam projections stay well defined (the
-        // source is outside the image).
-        const int line = xd ? tx0 + lane : ty0 + lane;
-        const bool ok = line < (xd ? a.nx : a.ny);
-        const int sb = xd ? ty0 : tx0;
-        const float fl = (float)line, f_lo = (float)(sb - 1), f_hi = (float)min(sb + kTH, xd ? a.ny : a.nx);
+        const int nline = xd ? a.nx : a.ny, ncross = xd ? a.ny : a.nx;
         const int *items = a.vitems + (xd ? 0 : a.nxv);
-        const int nitems = ok ? (xd ? a.nxv : a.nyv) : 0;
-        for (int it = z * G + g; it < nitems; it += G * nsplit) {
-            const int v = __ldg(items + it);
-            const ViewRec vr = a.views[v];
-            const long long vb = (long long)v * a.n_bins;
-            // detector projections of the strip's end points
-            const float nb = xd ? fmaf(vr.n1, fl, vr.n0) : fmaf(vr.n2, fl, vr.n0);
-            const float db = xd ? fmaf(vr.d1, fl, vr.d0) : fmaf(vr.d2, fl, vr.d0);
-            const float na = xd ? vr.n2 : vr.n1, da = xd ? vr.d2 : vr.d1;
-            int b0, b1;
-            seg_range<FAN>(fmaf(na, f_lo, nb), fmaf(da, f_lo, db), fmaf(na, f_hi, nb), fmaf(da, f_hi, db), vr.c,
-                           xd ? vr.xb0 : vr.yb0, xd ? vr.xb1 : vr.yb1, b0, b1);
-            strip_walk<FAN, DELTA, COHERENT>(a.rays + vb, a.walk + vb, a.r + vb, DELTA ? a.delta + vb : nullptr,
-                                             b0, b1, fl, (float)sb, al);
-        }
-        __syncthreads();
-        // fixed-order sum over the warps; pixel j of a lane's strip is its
-        // accumulator row j + 1.  The y-driven parts are read transposed (tile
-        // row = lane) so that consecutive threads read consecutive banks.
-        for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
-            const int i = t % kTW, k = t / kTW;
-            float s = 0.0f;
-            for (int q = 0; q < G; ++q) s += sm.acc[q][(k + 1) * kAccLd + i];
-            if (xd)
-                sm.stage[k][i] = s;   // column i, row k
-            else
-                sm.stage[i][k] += s;  // row i, column k
+        if constexpr (!PAIR) {
+            float *al = sm.acc[g] + lane;
+            for (int r = 0; r < kRows; ++r) al[r * kAccLd] = 0.0f;
+            // the lane's strip: x-driven rays, column tx0 + lane over rows ty0
+            // .. ty0 + kTH - 1; y-driven rays, row ty0 + lane over columns tx0
+            // .. tx0 + kTW - 1.  Its end points are kept within one pixel of
+            // the image so that their fan-beam projections stay well defined
+            // (the source is outside the image).
+            const int line = (xd ? tx0 : ty0) + lane;
+            const int sb = xd ? ty0 : tx0;
+            const float fl = (float)line, f_lo = (float)(sb - 1), f_hi = (float)min(sb + kTH, ncross);
+            const int nitems = line < nline ? (xd ? a.nxv : a.nyv) : 0;
+            for (int it = z * G + g; it < nitems; it += G * nsplit) {
+                const int v = __ldg(items + it);
+                const ViewRec vr = a.views[v];
+                const long long vb = (long long)v * a.n_bins;
+                // detector projections of the strip's end points
+                const float nb = xd ? fmaf(vr.n1, fl, vr.n0) : fmaf(vr.n2, fl, vr.n0);
+                const float db = xd ? fmaf(vr.d1, fl, vr.d0) : fmaf(vr.d2, fl, vr.d0);
+                const float na = xd ? vr.n2 : vr.n1, da = xd ? vr.d2 : vr.d1;
+                int b0, b1;
+                seg_range<FAN>(fmaf(na, f_lo, nb), fmaf(da, f_lo, db), fmaf(na, f_hi, nb), fmaf(da, f_hi, db), vr.c,
+                               xd ? vr.xb0 : vr.yb0, xd ? vr.xb1 : vr.yb1, b0, b1);
+                strip_walk<FAN, DELTA, COHERENT>(a.rays + vb, a.walk + vb, a.r + vb, DELTA ? a.delta + vb : nullptr,
+                                                 b0, b1, fl, (float)sb, al);
+            }
+            __syncthreads();
+            // fixed-order sum over the warps; pixel j of a lane's strip is its
+            // accumulator row j + 1.  The y-driven parts are read transposed
+            // (tile row = lane) so that consecutive threads read consecutive
+            // banks.
+            for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
+                const int i = t % kTW, k = t / kTW;
+                float s = 0.0f;
+                for (int q = 0; q < G; ++q) s += sm.acc[q][(k + 1) * kAccLd + i];
+                if (xd)
+                    sm.stage[k][i] = s;   // column i, row k
+                else
+                    sm.stage[i][k] += s;  // row i, column k
+            }
+        } else {
+            const int hf = lane >> 4, lp = lane & 15;  // cross-axis half, line pair
+            float *al0 = sm.acc[g] + hf * kHalfWords + ((2 * lp + hf) & 31);
+            float *al1 = sm.acc[g] + hf * kHalfWords + ((2 * lp + 1 + hf) & 31);
+            for (int r = 0; r < kRowsH; ++r) {
+                al0[r * kAccLd] = 0.0f;
+                al1[r * kAccLd] = 0.0f;
+            }
+            // the lane's strips: lines `line` and line + 1 over cross pixels
+            // sb .. sb + kHalf - 1, end points within one pixel of the image
+            const int line = (xd ? tx0 : ty0) + 2 * lp;
+            const int sb = (xd ? ty0 : tx0) + hf * kHalf;
+            const float fl = (float)line, f_lo = (float)(sb - 1), f_hi = (float)min(sb + kHalf, ncross);
+            const int nitems = (line < nline && sb < ncross) ? (xd ? a.nxv : a.nyv) : 0;
+            for (int it = z * G + g; it < nitems; it += G * nsplit) {
+                const int v = __ldg(items + it);
+                const ViewRec vr = a.views[v];
+                const long long vb = (long long)v * a.n_bins;
+                // detector projections of the four corners of the lane's strips
+                const float nl = xd ? vr.n1 : vr.n2, dl = xd ? vr.d1 : vr.d2;
+                const float na = xd ? vr.n2 : vr.n1, da = xd ? vr.d2 : vr.d1;
+                const float nb0 = fmaf(nl, fl, vr.n0), db0 = fmaf(dl, fl, vr.d0);
+                const float nb1 = fmaf(nl, fl + 1.0f, vr.n0), db1 = fmaf(dl, fl + 1.0f, vr.d0);
+                int b0, b1;
+                seg_range2<FAN>(fmaf(na, f_lo, nb0), fmaf(da, f_lo, db0), fmaf(na, f_hi, nb0), fmaf(da, f_hi, db0),
+                                fmaf(na, f_lo, nb1), fmaf(da, f_lo, db1), fmaf(na, f_hi, nb1), fmaf(da, f_hi, db1),
+                                vr.c, xd ? vr.xb0 : vr.yb0, xd ? vr.xb1 : vr.yb1, b0, b1);
+                strip_walk2<DELTA, COHERENT>(a.rays + vb, a.walk + vb, a.r + vb, DELTA ? a.delta + vb : nullptr, b0,
+                                             b1, fl, (float)sb, al0, al1);
+            }
+            __syncthreads();
+            // fixed-order sum over the warps: line i, cross pixel k of the
+            // tile is half h = k / kHalf, row k - h kHalf + 1, word (i + h)
+            // mod 32; the y-driven parts are written transposed
+            for (int t = threadIdx.x; t < kTH * kTW; t += G * 32) {
+                const int i = t % kTW, k = t / kTW, h = k / kHalf;
+                const int w = h * kHalfWords + (k - h * kHalf + 1) * kAccLd + ((i + h) & 31);
+                float s = 0.0f;
+                for (int q = 0; q < G; ++q) s += sm.acc[q][w];
+                if (xd)
+                    sm.stage[k][i] = s;
+                else
+                    sm.stage[i][k] += s;
+            }
         }
         __syncthreads();
     }
