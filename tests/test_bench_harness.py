@@ -70,3 +70,29 @@ def test_clock_summary_parsing(tmp_path):
     out = s.summary()
     assert out["sm_mhz"] == 1980 and out["sm_max_mhz"] == 2070
     assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 3
+
+
+def test_summaries_are_compact_and_complete():
+    """The batched and served summaries close the benchmark line: every number
+    a reader needs (per-form recon/s, latencies, PSNR, speed-up) in a few
+    hundred characters."""
+    import json
+
+    import bench
+    leg = {"recon_per_s": 10.0, "ms": 100.0, "p50_latency_ms": 50.0, "p99_latency_ms": 99.0, "mean_psnr_db": 30.0}
+    batched = {"jobs": 64, "iters_per_job": 100, "sequential": dict(leg), "batched": dict(leg),
+               "batched_graph": dict(leg), "speedup_vs_sequential": 1.9,
+               "policies": {name: dict(leg) for name in bench.BATCH_POLICIES},
+               "tuning": {"batch_policy": bench.BATCH_POLICIES[2], "plan_adj_splits": [2, 8]}}
+    b = bench.batched_summary(batched)
+    assert b["policy"] == bench.BATCH_POLICIES[2]
+    assert len(b["recon_per_s"]["per_policy"]) == len(bench.BATCH_POLICIES) == 3
+    assert set(b["recon_per_s"]) >= {"sequential", "batched", "graph"}
+    served_leg = {"recon_per_s": 1.0, "p50_latency_s": 2.0, "p99_latency_s": 3.0, "mean_psnr_db": 30.0,
+                  "mean_iters": 100.0}
+    served = {"requests": 16, "ranges": "128..1024^2, 90..1440 views, tol 0.0001", "sequential_capacity_per_s": 1.0,
+              "loads": [{"load_vs_sequential_capacity": 1.5, "served": dict(served_leg),
+                         "sequential": dict(served_leg), "speedup_recon_per_s": 1.03}]}
+    v = bench.served_summary(served)
+    assert v["load_1.5"]["speedup"] == 1.03 and v["ranges"].startswith("128..1024")
+    assert len(json.dumps(b)) + len(json.dumps(v)) < 900
