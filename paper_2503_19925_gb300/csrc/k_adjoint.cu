@@ -14,7 +14,9 @@
 //   - then the views with y-driven rays: lane l owns row ty0 + l and walks its
 //     rays the same way.
 // Warp g of split z takes items z kG + g + k kG nsplit of each list, so the
-// splits interleave over the views.
+// splits interleave over the views.  Fan beams walk line pairs instead: lane l
+// owns lines 2 (l % 16) and the next over half l / 16 of the strip, so one
+// step along a ray (its residual, its reciprocal) serves two crossings.
 // The rays crossing a strip form one contiguous bin range: the two end points
 // of the strip projected onto the detector (a ratio of affine forms of the
 // pixel coordinates, stored per view) bound it.  Each lane accumulates into
