@@ -108,6 +108,10 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
         bits = a.bits[i];
     }
     const int jlo = ray_jlo(bits), jhi = ray_jhi(bits);
+    // chunks the ray samples: cfirst .. cfirst + cspan (an empty range gets a
+    // first chunk no unit reaches, so the unsigned test below always fails)
+    const int cfirst = jlo <= jhi ? jlo / kFC : 0x3fffffff;
+    const int cspan = jlo <= jhi ? jhi / kFC - jlo / kFC : 0;
     const CUtensorMap *map = u.axis ? map_r : map_c;
     const int A = (int)rec.A;
     const int *kst = a.kstart + u.koff;
@@ -164,7 +168,7 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
         }
         const int j0 = (u.jc0 + c) * kFC;
         // the ray samples this chunk (an empty range, j_lo > j_hi, never does)
-        if (max(jlo, j0) <= min(jhi, j0 + kFC - 1)) {
+        if ((unsigned)(u.jc0 + c - cfirst) <= (unsigned)cspan) {
             // anchor: t(j0) = K + tau0 with tau0 accurate to FP32 rounding at ~1
             const float jf = (float)j0;
             const float p = rec.bh * jf;
@@ -185,8 +189,9 @@ __device__ __forceinline__ bool forward_unit(const FwdArgs &a, int ui, const CUt
             const float tl = fmaf(rec.bh, (float)(kFC - 1), tau0);
             const int rf = off + __float_as_int(__fadd_rd(tau0, kFloorMagic));
             const int rl = off + __float_as_int(__fadd_rd(tl, kFloorMagic));
-            const bool inside = fabsf(tau0) < 4194304.0f && fabsf(tl) < 4194304.0f &&
-                                (unsigned)rf <= (unsigned)(kFHB - 2) && (unsigned)rl <= (unsigned)(kFHB - 2);
+            // (a crossing that is NaN, infinite or below -2^23 gives a row far
+            // outside the band, so the two row tests also cover those)
+            const bool inside = (unsigned)rf <= (unsigned)(kFHB - 2) && (unsigned)rl <= (unsigned)(kFHB - 2);
             if (inside) {
                 const float *sb = sm.buf[b] + off;  // + bits(r) lands in the buffer
 #pragma unroll
