@@ -1,7 +1,7 @@
 // k_adjoint.cu -- adjoint g = A^T r of the Joseph projector of k_forward.cu,
 // as a deterministic gather (fixed summation order, no atomics), with the
-// fused extragradient epilogue of Eq. (11) and the FP64 partial norms of the
-// stopping rule.
+// fused extragradient epilogue of Eq. (11) and the per-tile FP64 partial norms
+// of the stopping rule (FP32 within a thread's few pixels).
 //
 // FP32 kernel (hot path, body in joseph.cuh): one CTA owns a tile of kTW x kTH
 // (32 x 32) pixels and, with a view split, one of its nsplit view subsets.  Its
