@@ -1,6 +1,7 @@
-"""Batched solves against single solves and the oracle, under policy 0 (one
-persistent launch for all jobs) and policy 2 (each job's own solve on one of
-the batch context's streams): a job's result is bitwise the same alone and in
+"""Batched solves against single solves and the oracle, under policies 0 and 1
+(one persistent launch for all jobs, one CTA per adjoint tile or each plan's
+view split) and policy 2 (each job's own solve on one of the batch context's
+streams): a job's result is bitwise the same alone and in
 any mix, matches the single-job path (bit for bit under policy 2) and the FP64
 oracle within the solve tolerances, and replays from a captured CUDA graph."""
 import math
@@ -52,7 +53,7 @@ def _jobs(mix, iters, idx=None, **kw):
                    iters=iters[k] if isinstance(iters, (list, tuple)) else iters, **kw) for k in idx]
 
 
-POLICIES = [0, 2]
+POLICIES = [0, 1, 2]
 
 
 def _batch(n, policy):
