@@ -458,9 +458,10 @@ int max_split(const Plan &P)
 }
 
 // View split of a new plan's adjoint, before any autotuning: the largest
-// candidate that keeps tiles x split within about 14 CTAs per SM (two waves
-// of the 7 adjoint CTAs resident per SM; larger splits measured no faster at
-// 512^2).  Small images get more CTAs than they have tiles.
+// candidate that keeps tiles x split within about 14 CTAs per SM (near three
+// waves of the 5 adjoint CTAs resident per SM; at 512^2 split 8, the largest
+// such, measured faster than 4 and 16).  Small images get more CTAs than they
+// have tiles.
 int default_split(const Plan &P)
 {
     const long long tiles = adjoint_blocks(P.g.nx, P.g.ny), want = 14LL * device_sms(P.device);

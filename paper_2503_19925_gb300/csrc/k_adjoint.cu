@@ -44,10 +44,10 @@ namespace exact {
 
 namespace {
 
-constexpr int kG = 6;  // warps per CTA of the per-plan kernel (one view at a time each)
+constexpr int kG = 8;  // warps per CTA of the per-plan kernel (one view at a time each)
 
 template <int MODE, bool FAN, bool DELTA>
-__global__ void __launch_bounds__(kG * 32, 7) k_adjoint(AdjArgs a)
+__global__ void __launch_bounds__(kG * 32, 5) k_adjoint(AdjArgs a)
 {
     if (a.state && a.state->done) return;
     extern __shared__ __align__(16) unsigned char adj_smem[];
