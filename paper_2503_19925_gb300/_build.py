@@ -68,7 +68,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         with ThreadPoolExecutor(max_workers=min(8, len(sources()))) as ex:
             objs = list(ex.map(compile_one, sources()))
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]  # plan tables are built on host threads
         proc = subprocess.run(cmd, capture_output=True, text=True)
         if proc.returncode != 0:
             raise RuntimeError(f"link failed:\n{proc.stderr}")

@@ -7,6 +7,7 @@
 #include <map>
 #include <atomic>
 #include <mutex>
+#include <thread>
 
 #include <climits>
 #include <cudaTypedefs.h>
@@ -248,11 +249,43 @@ bool make_unit(const RayF *rf, const int *bits, long long ray0, int cnt, int axi
     return true;
 }
 
-// Splits every view segment into work units of at most kFR rays whose bands fit.
-bool build_units(const exact_geometry &g, const std::vector<RayF> &rf, const std::vector<int> &rbits,
-                 const std::vector<ViewRec> &vw, std::vector<FwdUnit> &units, std::vector<int> &kst)
+// Host threads for building a plan's tables: one for small plans, up to 16
+// for plans of 64 K rays or more (the per-view work is independent).
+int table_threads(long long n_rays)
 {
-    for (int v = 0; v < g.n_views; ++v) {
+    if (n_rays < (1LL << 16)) return 1;
+    const unsigned hw = std::thread::hardware_concurrency();
+    return hw < 2 ? 1 : (hw > 16 ? 16 : (int)hw);
+}
+
+// body(v) for v in [0, n) on `threads` host threads (views interleaved).
+template <class F>
+void parallel_views(int n, int threads, const F &body)
+{
+    if (threads <= 1 || n <= 1) {
+        for (int v = 0; v < n; ++v) body(v);
+        return;
+    }
+    const int T = threads < n ? threads : n;
+    std::vector<std::thread> pool;
+    pool.reserve((size_t)T);
+    for (int t = 0; t < T; ++t)
+        pool.emplace_back([&body, n, T, t] {
+            for (int v = t; v < n; v += T) body(v);
+        });
+    for (std::thread &th : pool) th.join();
+}
+
+// Splits every view segment into work units of at most kFR rays whose bands
+// fit.  Views are split independently (on `threads` host threads) and
+// concatenated in view order, so the tables do not depend on the threads.
+bool build_units(const exact_geometry &g, const std::vector<RayF> &rf, const std::vector<int> &rbits,
+                 const std::vector<ViewRec> &vw, std::vector<FwdUnit> &units, std::vector<int> &kst, int threads)
+{
+    std::vector<std::vector<FwdUnit>> vu((size_t)g.n_views);
+    std::vector<std::vector<int>> vk((size_t)g.n_views);
+    std::atomic<bool> ok{true};
+    parallel_views(g.n_views, threads, [&](int v) {
         const long long vb = (long long)v * g.n_bins;
         const int segs[2][3] = {{vw[v].xb0, vw[v].xb1, 0}, {vw[v].yb0, vw[v].yb1, 1}};
         for (const auto &sg : segs) {
@@ -260,14 +293,26 @@ bool build_units(const exact_geometry &g, const std::vector<RayF> &rf, const std
             while (b < sg[1]) {
                 int cnt = sg[1] - b < kFR ? sg[1] - b : kFR;
                 FwdUnit u;
-                while (!make_unit(rf.data(), rbits.data(), vb + b, cnt, sg[2], u, kst)) {
-                    if (cnt == 1) return false;
+                while (!make_unit(rf.data(), rbits.data(), vb + b, cnt, sg[2], u, vk[v])) {
+                    if (cnt == 1) {
+                        ok = false;
+                        return;
+                    }
                     cnt = cnt * 3 / 4 > 1 ? cnt * 3 / 4 : 1;
                 }
-                units.push_back(u);
+                vu[v].push_back(u);
                 b += cnt;
             }
         }
+    });
+    if (!ok) return false;
+    for (int v = 0; v < g.n_views; ++v) {
+        const int base = (int)kst.size();  // the view's band starts follow the earlier views'
+        for (FwdUnit u : vu[v]) {
+            u.koff += base;
+            units.push_back(u);
+        }
+        kst.insert(kst.end(), vk[v].begin(), vk[v].end());
     }
     return true;
 }
@@ -770,7 +815,9 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
     std::vector<float> rdelta((size_t)P->n);
     std::vector<RayD> rd((size_t)P->n);
     std::vector<ViewRec> vw((size_t)g.n_views);
-    for (int v = 0; v < g.n_views; ++v) {
+    const int threads = table_threads(P->n);
+    std::atomic<bool> axis_ok{true};
+    parallel_views(g.n_views, threads, [&](int v) {
         int switches = 0;
         int prev_axis = -1;
         int first_axis = -1, sw = g.n_bins;
@@ -803,8 +850,8 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
             prev_axis = h.axis;
         }
         if (switches > 1) {  // driving axis must switch at most once per view (fan angle below 90 degrees)
-            delete P;
-            return EXACT_ERR_UNSUPPORTED;
+            axis_ok = false;
+            return;
         }
         // segment [0, sw) has first_axis, [sw, n_bins) the other one
         int xb0 = 0, xb1 = 0, yb0 = 0, yb1 = 0;
@@ -814,10 +861,14 @@ exact_status exact_plan_create(const exact_geometry *geometry, const exact_spect
             yb0 = 0; yb1 = sw; xb0 = sw; xb1 = g.n_bins;
         }
         vw[v] = make_view(g, v, xb0, xb1, yb0, yb1);
+    });
+    if (!axis_ok) {
+        delete P;
+        return EXACT_ERR_UNSUPPORTED;
     }
     std::vector<FwdUnit> units;
     std::vector<int> kst;
-    if (!build_units(g, rf, rbits, vw, units, kst)) {
+    if (!build_units(g, rf, rbits, vw, units, kst, threads)) {
         delete P;
         return EXACT_ERR_UNSUPPORTED;
     }
